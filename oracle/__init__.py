@@ -1,0 +1,285 @@
+"""CPU FP64 oracle for the Krylov-space Green's-function method.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+baseline legs of bench.py may import this package.  The CUDA library never
+calls it, and it shares no code, table or helper with the CUDA path.
+
+The heavy loops live in kg_oracle.cpp (basis, H*psi, c/c^dag, Lanczos ground
+state, Chebyshev propagator).  This module assembles the Green's functions
+exactly as the paper defines them:
+
+* equilibrium, Section 3, Eqs. (psit) and (psigreen), plus the hole part
+  given after Eq. (gomega):
+      G^>_{aa'}(t) = -i e^{+i E0 t} < c^dag_a 0 | e^{-iHt} | c^dag_a' 0 >
+      G^<_{aa'}(t) = +i e^{-i E0 t} < c_a' 0 | e^{+iHt} | c_a 0 >
+  (eta = 0; the retarded function is G^> - G^< for t >= 0);
+* nonequilibrium, Section 4, steps (i)-(iv):
+      |0> = ground state of H_ini, Phi(t) = e^{-iHt}|0>,
+      Psi_a(t) = e^{iHt} c_a Phi(t),  chi_a(t) = e^{iHt} c^dag_a Phi(t),
+      G^<_{aa'}(t,t') = i <Psi_a'(t') | Psi_a(t)>,
+      G^>_{aa'}(t,t') = -i <chi_a(t) | chi_a'(t')>.
+
+Every propagation here is a Chebyshev expansion over the whole interval
+(never the GPU's restarted Krylov steps), so the two sides are independent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kg_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "libkgoracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile the C++ oracle into oracle/_build/libkgoracle.so with g++."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ko_model_new.restype = P
+    lib.ko_model_new.argtypes = [I, I, I, P, P, P, P]
+    lib.ko_model_free.argtypes = [P]
+    lib.ko_model_dim.restype = ctypes.c_long
+    lib.ko_model_dim.argtypes = [P]
+    lib.ko_model_basis.argtypes = [P, P]
+    lib.ko_model_bounds.argtypes = [P, P, P]
+    lib.ko_num_threads.restype = I
+    lib.ko_set_num_threads.argtypes = [I]
+    lib.ko_hpsi.argtypes = [P, P, P]
+    lib.ko_apply_cop.restype = I
+    lib.ko_apply_cop.argtypes = [P, P, I, I, I, P, P]
+    lib.ko_ground_state.restype = I
+    lib.ko_ground_state.argtypes = [P, I, I, D, ctypes.c_ulonglong, P, P, P]
+    lib.ko_propagate.restype = I
+    lib.ko_propagate.argtypes = [P, P, D, P]
+    _lib = lib
+    return lib
+
+
+def num_threads():
+    return _load().ko_num_threads()
+
+
+def set_num_threads(n):
+    _load().ko_set_num_threads(int(n))
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Sector:
+    """One (N_up, N_dn) sector of a model (see workloads.make_model)."""
+
+    def __init__(self, model, n_up=None, n_dn=None):
+        lib = _load()
+        self.model = model
+        self.L = model["L"]
+        self.n_up = model["n_up"] if n_up is None else n_up
+        self.n_dn = model["n_dn"] if n_dn is None else n_dn
+        self._h_re = np.ascontiguousarray(model["h"].real, dtype=np.float64)
+        self._h_im = np.ascontiguousarray(model["h"].imag, dtype=np.float64)
+        self._eps = np.ascontiguousarray(model["eps"], dtype=np.float64)
+        self._U = np.ascontiguousarray(model["U"], dtype=np.float64)
+        self.h = lib.ko_model_new(self.L, self.n_up, self.n_dn, _ptr(self._h_re), _ptr(self._h_im),
+                                  _ptr(self._eps), _ptr(self._U))
+        if not self.h:
+            raise ValueError("invalid sector")
+        self.dim = int(lib.ko_model_dim(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ko_model_free(self.h)
+            self.h = None
+
+    def basis(self):
+        out = np.empty(self.dim, dtype=np.uint64)
+        _load().ko_model_basis(self.h, _ptr(out))
+        return out
+
+    def bounds(self):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        _load().ko_model_bounds(self.h, ctypes.byref(lo), ctypes.byref(hi))
+        return lo.value, hi.value
+
+    def hpsi(self, x):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.empty_like(x)
+        _load().ko_hpsi(self.h, _ptr(x), _ptr(y))
+        return y
+
+    def neighbour(self, spin, dagger):
+        du = (1 if dagger else -1) if spin == 0 else 0
+        dd = (1 if dagger else -1) if spin == 1 else 0
+        nu, nd = self.n_up + du, self.n_dn + dd
+        if nu < 0 or nd < 0 or nu > self.L or nd > self.L:
+            return None
+        return Sector(self.model, nu, nd)
+
+    def apply_cop(self, dst, site, spin, dagger, x):
+        """y = c_{site,spin} x (dagger False) or c^dag x, y in sector dst."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.empty(dst.dim, dtype=np.complex128)
+        rc = _load().ko_apply_cop(self.h, dst.h, site, spin, 1 if dagger else 0, _ptr(x), _ptr(y))
+        if rc != 0:
+            raise ValueError("bad sector pair for c/c^dag")
+        return y
+
+    def ground_state(self, K=80, max_restarts=60, tol=1e-12, seed=1234):
+        """(E0, |0>, residual) by restarted Lanczos with full reorthogonalisation."""
+        psi = np.empty(self.dim, dtype=np.complex128)
+        e0, res = ctypes.c_double(), ctypes.c_double()
+        rc = _load().ko_ground_state(self.h, K, max_restarts, tol, seed, ctypes.byref(e0), _ptr(psi),
+                                     ctypes.byref(res))
+        if rc < 0:
+            raise ValueError("empty sector")
+        return e0.value, psi, res.value
+
+    def propagate(self, x, tau):
+        """exp(-i H tau) x (tau may be negative) by a Chebyshev expansion."""
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        y = np.empty_like(x)
+        _load().ko_propagate(self.h, _ptr(x), float(tau), _ptr(y))
+        return y
+
+
+def _groups(orbitals):
+    return {s: [k for k, (_, sp) in enumerate(orbitals) if sp == s] for s in (0, 1)}
+
+
+def green_equilibrium(model, orbitals, dt, n_steps, gs=None, K=80, tol=1e-12):
+    """Equilibrium G^>(t_k), G^<(t_k) for t_k = k*dt, k = 0..n_steps.
+
+    Returns (G_gtr, G_les, E0), each G of shape [n_steps+1, n_orb, n_orb]
+    (complex) with G[k, a, a'] = G_{a a'}(t_k).  Entries with different spins
+    vanish (S_z is conserved).  Time stepping uses exp(-iH dt) repeatedly, each
+    step one Chebyshev expansion (Section 3, Eq. (psigreen) with eta = 0).
+    """
+    sec = Sector(model)
+    E0, psi0, _ = sec.ground_state(K=K, tol=tol) if gs is None else gs
+    n = len(orbitals)
+    t = dt * np.arange(n_steps + 1)
+    G_gtr = np.zeros((n_steps + 1, n, n), dtype=np.complex128)
+    G_les = np.zeros_like(G_gtr)
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger, G in ((True, G_gtr), (False, G_les)):
+            nb = sec.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            vecs = {a: sec.apply_cop(nb, orbitals[a][0], spin, dagger, psi0) for a in idx}
+            for p in idx:
+                # particle part: cur = e^{-iHt} c^dag_p |0>, and
+                #   G^>_{a p}(t) = -i e^{iE0 t} <c^dag_a 0 | cur>;
+                # hole part: cur = e^{+iHt} c_p |0>, and
+                #   G^<_{p a}(t) = +i e^{-iE0 t} <c_a 0 | cur>.
+                cur = vecs[p].copy()
+                for k in range(n_steps + 1):
+                    for a in idx:
+                        ov = np.vdot(vecs[a], cur)
+                        if dagger:
+                            G[k, a, p] = -1j * np.exp(1j * E0 * t[k]) * ov
+                        else:
+                            G[k, p, a] = 1j * np.exp(-1j * E0 * t[k]) * ov
+                    if k < n_steps:
+                        cur = nb.propagate(cur, dt if dagger else -dt)
+    return G_gtr, G_les, E0
+
+
+def keldysh_vectors(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):
+    """Steps (i)-(iii) of Section 4: returns (E0, Phi, Psi, Chi).
+
+    Phi[k] = e^{-iH t_k}|0>, Psi[s][k][a] = e^{iH t_k} c_a Phi(t_k) and
+    Chi[s][k][a] = e^{iH t_k} c^dag_a Phi(t_k) for the orbitals of spin s.
+    Each back-propagation is one Chebyshev expansion over the full time t_k.
+    """
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    sec_f = Sector(fin)
+    t = dt * np.arange(n_t)
+    Phi = [psi0.copy()]
+    for k in range(1, n_t):
+        Phi.append(sec_f.propagate(Phi[-1], dt))
+    Psi, Chi = {}, {}
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger, store in ((False, Psi), (True, Chi)):
+            nb = sec_f.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            store[spin] = [[nb.propagate(sec_f.apply_cop(nb, orbitals[a][0], spin, dagger, Phi[k]), -t[k])
+                            for a in idx] for k in range(n_t)]
+    return E0, Phi, Psi, Chi
+
+
+def green_keldysh(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):
+    """G^<(t_k,t_l), G^>(t_k,t_l) of Section 4, shape [n_t, n_t, n_orb, n_orb].
+
+    G[k, l, a, a'] = G_{a a'}(t_k, t_l); step (iv) is a plain Gram matrix.
+    """
+    E0, Phi, Psi, Chi = keldysh_vectors(ini, fin, orbitals, dt, n_t, gs=gs, K=K, tol=tol)
+    n = len(orbitals)
+    G_les = np.zeros((n_t, n_t, n, n), dtype=np.complex128)
+    G_gtr = np.zeros_like(G_les)
+    for spin, idx in _groups(orbitals).items():
+        if spin in Psi:
+            for k in range(n_t):
+                for l in range(n_t):
+                    for ia, a in enumerate(idx):
+                        for ib, b in enumerate(idx):
+                            G_les[k, l, a, b] = 1j * np.vdot(Psi[spin][l][ib], Psi[spin][k][ia])
+        if spin in Chi:
+            for k in range(n_t):
+                for l in range(n_t):
+                    for ia, a in enumerate(idx):
+                        for ib, b in enumerate(idx):
+                            G_gtr[k, l, a, b] = -1j * np.vdot(Chi[spin][k][ia], Chi[spin][l][ib])
+    return G_les, G_gtr, E0
+
+
+def keldysh_entry(ini, fin, orbital_a, orbital_b, dt, k, l, gs=None, K=80, tol=1e-12):
+    """One sampled pair (G^<_{ab}(t_k,t_l), G^>_{ab}(t_k,t_l)) at any size.
+
+    Only Phi(t_k), Phi(t_l) and four back-propagated vectors are formed, so a
+    single entry of a large Keldysh grid can be checked one by one.
+    """
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    sec_f = Sector(fin)
+    (sa, pa), (sb, pb) = orbital_a, orbital_b
+    if pa != pb:
+        return 0j, 0j
+    tk, tl = dt * k, dt * l
+    phi_k = sec_f.propagate(psi0, tk) if k else psi0
+    phi_l = sec_f.propagate(psi0, tl) if l else psi0
+    out = []
+    for dagger in (False, True):
+        nb = sec_f.neighbour(pa, dagger)
+        if nb is None:
+            out.append(0j)
+            continue
+        va = nb.propagate(sec_f.apply_cop(nb, sa, pa, dagger, phi_k), -tk)
+        vb = nb.propagate(sec_f.apply_cop(nb, sb, pb, dagger, phi_l), -tl)
+        out.append(1j * np.vdot(vb, va) if not dagger else -1j * np.vdot(va, vb))
+    return out[0], out[1]

@@ -1,0 +1,403 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+* brute force: a dense Fock-space Hamiltonian built from Jordan-Wigner
+  matrices with numpy Kronecker products (an independent construction of the
+  second-quantised operators) on L <= 5;
+* library routines: numpy eigh and scipy expm on those dense matrices;
+* closed forms: U = 0 free fermions (single-particle h), the Hubbard atom;
+* invariants: sum rule, hermiticity, particle-hole symmetry, particle number,
+  the equal-time values the paper states for its Fig. 2 and Fig. 4 models.
+
+Each plausible mistake (a dropped term, a wrong sign or index, a transposed
+operand, a conjugate missing) fails at least one of these.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ dense JW tools
+def jw_annihilators(n_modes):
+    """Dense c_m on the 2^n Fock space, basis index = sum_m n_m 2^m."""
+    dim = 1 << n_modes
+    occ = ((np.arange(dim)[:, None] >> np.arange(n_modes)[None, :]) & 1)
+    out = []
+    for m in range(n_modes):
+        c = np.zeros((dim, dim))
+        for k in range(dim):
+            if occ[k, m]:
+                sgn = (-1) ** int(occ[k, :m].sum())
+                c[k ^ (1 << m), k] = sgn
+        out.append(c)
+    return out
+
+
+def jw_parts(L):
+    c = jw_annihilators(2 * L)
+    return c
+
+
+def dense_fock_h(model, c):
+    L = model["L"]
+    dim = c[0].shape[0]
+    H = np.zeros((dim, dim), dtype=np.complex128)
+    h, eps, U = model["h"], model["eps"], model["U"]
+    for s in range(2):
+        for i in range(L):
+            ci = c[s * L + i]
+            H += (eps[s, i] + h[i, i].real) * (ci.T @ ci)
+            for j in range(L):
+                if i != j and h[i, j] != 0:
+                    H += h[i, j] * (ci.T @ c[s * L + j])
+    for i in range(L):
+        H += U[i] * (c[i].T @ c[i]) @ (c[L + i].T @ c[L + i])
+    return H
+
+
+def sector_index(L, nu, nd):
+    dim = 1 << (2 * L)
+    k = np.arange(dim)
+    up = np.array([bin(x & ((1 << L) - 1)).count("1") for x in k])
+    dn = np.array([bin(x >> L).count("1") for x in k])
+    return np.nonzero((up == nu) & (dn == nd))[0]  # ascending = sorted states
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+# --------------------------------------------------------------- basis pins
+@pytest.mark.parametrize("L,nu,nd", [(4, 2, 2), (5, 2, 3), (6, 1, 5), (7, 3, 3)])
+def test_basis_order_and_size(L, nu, nd):
+    s = oracle.Sector(W.hubbard_ring(L, 1.0, nu, nd))
+    b = s.basis()
+    assert s.dim == math.comb(L, nu) * math.comb(L, nd)
+    assert np.all(np.diff(b.astype(np.float64)) > 0)
+    ups = sorted(x for x in range(1 << L) if bin(x).count("1") == nu)
+    dns = sorted(x for x in range(1 << L) if bin(x).count("1") == nd)
+    Du = len(ups)
+    for idx in range(0, s.dim, max(1, s.dim // 50)):
+        assert int(b[idx]) == ups[idx % Du] | (dns[idx // Du] << L)
+
+
+# ---------------------------------------------------------- H*psi and c/c^dag
+@pytest.mark.parametrize("L", [2, 3, 4, 5])
+def test_hpsi_vs_jordan_wigner(L):
+    c = jw_parts(L)
+    rng = np.random.default_rng(L)
+    for seed in range(3):
+        nu, nd = int(rng.integers(0, L + 1)), int(rng.integers(0, L + 1))
+        m = W.random_model(L, nu, nd, seed=100 * L + seed, complex_hopping=True)
+        H = dense_fock_h(m, c)
+        idx = sector_index(L, nu, nd)
+        Hs = H[np.ix_(idx, idx)]
+        assert np.allclose(Hs, Hs.conj().T)
+        s = oracle.Sector(m)
+        x = W.random_state(s.dim, seed)
+        assert rel(s.hpsi(x), Hs @ x) < 1e-13
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_cop_vs_jordan_wigner(L):
+    c = jw_parts(L)
+    m = W.random_model(L, 1, 2, seed=7)
+    for spin in (0, 1):
+        for site in range(L):
+            for dagger in (False, True):
+                src = oracle.Sector(W.with_sector(m, 1, 2))
+                dst = src.neighbour(spin, dagger)
+                if dst is None:
+                    continue
+                op = c[spin * L + site]
+                op = op.T if dagger else op
+                i_src = sector_index(L, 1, 2)
+                i_dst = sector_index(L, dst.n_up, dst.n_dn)
+                x = W.random_state(src.dim, site + 10 * spin)
+                ref = op[np.ix_(i_dst, i_src)] @ x
+                assert np.max(np.abs(src.apply_cop(dst, site, spin, dagger, x) - ref)) < 1e-15
+
+
+def test_hpsi_hermitian_larger():
+    m = W.random_model(8, 3, 4, seed=3)
+    s = oracle.Sector(m)
+    x, y = W.random_state(s.dim, 1), W.random_state(s.dim, 2)
+    assert abs(np.vdot(x, s.hpsi(y)) - np.vdot(s.hpsi(x), y)) < 1e-12
+
+
+# ------------------------------------------------------------- ground state
+@pytest.mark.parametrize("L,nu,nd,seed", [(4, 2, 2, 1), (5, 2, 3, 2), (5, 3, 3, 3)])
+def test_ground_state_vs_eigh(L, nu, nd, seed):
+    c = jw_parts(L)
+    m = W.random_model(L, nu, nd, seed=seed, complex_hopping=True)
+    idx = sector_index(L, nu, nd)
+    Hs = dense_fock_h(m, c)[np.ix_(idx, idx)]
+    w, v = np.linalg.eigh(Hs)
+    E0, psi, res = oracle.Sector(m).ground_state()
+    assert abs(E0 - w[0]) <= 1e-13 * max(1, abs(w[0]))
+    assert abs(abs(np.vdot(v[:, 0], psi)) - 1) < 1e-12
+    assert res < 1e-12 * max(1, abs(E0))
+
+
+def free_fermion_e0(h, eps_s, n):
+    w = np.linalg.eigvalsh(h + np.diag(eps_s))
+    return w[:n].sum(), w
+
+
+def test_ground_state_U0_closed_form():
+    # open chain L = 10 at half filling: single-particle levels -2cos(k pi/11)
+    # are nondegenerate, so the Slater determinant ground state is unique.
+    L = 10
+    m = W.make_model(L, 5, 5, W.chain_hopping(L), np.vstack([np.linspace(-0.3, 0.2, L)] * 2), np.zeros(L))
+    E_up, _ = free_fermion_e0(m["h"], m["eps"][0], 5)
+    E_dn, _ = free_fermion_e0(m["h"], m["eps"][1], 5)
+    E0, _, _ = oracle.Sector(m).ground_state()
+    assert abs(E0 - (E_up + E_dn)) < 1e-12 * abs(E_up + E_dn)
+
+
+def test_hubbard_atom_energies():
+    U, e = 3.0, -1.2
+    for nu, nd, ref in [(0, 0, 0.0), (1, 0, e), (0, 1, e), (1, 1, 2 * e + U)]:
+        m = W.make_model(1, nu, nd, np.zeros((1, 1)), np.array([[e], [e]]), np.array([U]))
+        E0, _, _ = oracle.Sector(m).ground_state()
+        assert abs(E0 - ref) < 1e-14
+
+
+# --------------------------------------------------------------- propagation
+@pytest.mark.parametrize("tau", [0.05, 0.7, -2.3])
+def test_propagate_vs_expm(tau):
+    L = 4
+    c = jw_parts(L)
+    m = W.random_model(L, 2, 1, seed=11, complex_hopping=True)
+    idx = sector_index(L, 2, 1)
+    Hs = dense_fock_h(m, c)[np.ix_(idx, idx)]
+    s = oracle.Sector(m)
+    x = W.random_state(s.dim, 5)
+    ref = sla.expm(-1j * tau * Hs) @ x
+    assert np.max(np.abs(s.propagate(x, tau) - ref)) < 1e-13
+
+
+def test_propagate_norm_and_reversal():
+    s = oracle.Sector(W.hubbard_ring(8, 4.0, 4, 3))
+    x = W.random_state(s.dim, 9)
+    y = s.propagate(x, 3.0)
+    assert abs(np.linalg.norm(y) - 1) < 1e-13
+    assert np.max(np.abs(s.propagate(y, -3.0) - x)) < 1e-13
+    # stepping agrees with one long expansion (group property)
+    z = x
+    for _ in range(6):
+        z = s.propagate(z, 0.5)
+    assert np.max(np.abs(z - y)) < 1e-12
+
+
+# ------------------------------------------------------ equilibrium G pins
+def dense_sector(m, c, nu, nd):
+    idx = sector_index(m["L"], nu, nd)
+    return idx, dense_fock_h(W.with_sector(m, nu, nd), c)[np.ix_(idx, idx)]
+
+
+def test_green_equilibrium_vs_dense_lehmann():
+    L = 4
+    c = jw_parts(L)
+    m = W.random_model(L, 2, 2, seed=21, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (1, 1), (3, 1)]
+    dt, n = 0.1, 12
+    Gg, Gl, E0 = oracle.green_equilibrium(m, orbs, dt, n)
+    Hfull = dense_fock_h(m, c)
+    i0 = sector_index(L, 2, 2)
+    w, v = np.linalg.eigh(Hfull[np.ix_(i0, i0)])
+    assert abs(E0 - w[0]) < 1e-12
+    g = np.zeros(Hfull.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    t = dt * np.arange(n + 1)
+    for k in range(n + 1):
+        U_t = sla.expm(-1j * t[k] * Hfull)
+        for a, (ia, sa) in enumerate(orbs):
+            for b, (ib, sb) in enumerate(orbs):
+                ca, cb = c[sa * L + ia], c[sb * L + ib]
+                ref_g = -1j * np.exp(1j * w[0] * t[k]) * (g.conj() @ ca @ U_t @ cb.T @ g)
+                ref_l = 1j * np.exp(-1j * w[0] * t[k]) * (g.conj() @ cb.T @ U_t.conj().T @ ca @ g)
+                assert abs(Gg[k, a, b] - ref_g) < 1e-12
+                assert abs(Gl[k, a, b] - ref_l) < 1e-12
+
+
+def test_green_equilibrium_U0_closed_form():
+    # complex Hermitian hopping, so a transposed or unconjugated density
+    # matrix rho[k, l] = <c^dag_l c_k> = (V V^dag)[k, l] would fail here.
+    L = 8
+    m = W.random_model(L, 4, 3, seed=5, complex_hopping=True)
+    m["U"][:] = 0.0
+    eps = m["eps"]
+    orbs = [(i, 0) for i in range(0, L, 2)] + [(1, 1), (4, 1)]
+    dt, n = 0.2, 10
+    Gg, Gl, _ = oracle.green_equilibrium(m, orbs, dt, n)
+    for spin, N in ((0, 4), (1, 3)):
+        hs = m["h"] + np.diag(eps[spin])
+        w, v = np.linalg.eigh(hs)
+        assert w[N] - w[N - 1] > 1e-3  # closed shell
+        rho = v[:, :N] @ v[:, :N].conj().T
+        idx = [k for k, o in enumerate(orbs) if o[1] == spin]
+        for k in range(n + 1):
+            U_t = sla.expm(-1j * hs * dt * k)
+            ref_g = -1j * U_t @ (np.eye(L) - rho)
+            ref_l = 1j * U_t @ rho
+            for a in idx:
+                for b in idx:
+                    i, j = orbs[a][0], orbs[b][0]
+                    assert abs(Gg[k, a, b] - ref_g[i, j]) < 1e-12
+                    assert abs(Gl[k, a, b] - ref_l[i, j]) < 1e-12
+    # opposite spins never mix
+    assert np.all(Gg[:, :4, 4:] == 0) and np.all(Gl[:, 4:, :4] == 0)
+
+
+def test_hubbard_atom_two_poles():
+    # half-filled atom, eps = -U/2: spin-averaged G^R(t) = -i cos(U t / 2).
+    U = 2.6
+    dt, n = 0.25, 16
+    t = dt * np.arange(n + 1)
+    GR = 0
+    for nu, nd in ((1, 0), (0, 1)):
+        m = W.make_model(1, nu, nd, np.zeros((1, 1)), np.full((2, 1), -U / 2), np.array([U]))
+        Gg, Gl, _ = oracle.green_equilibrium(m, [(0, 0), (0, 1)], dt, n)
+        GR = GR + 0.5 * (Gg - Gl)
+    avg = 0.5 * (GR[:, 0, 0] + GR[:, 1, 1])
+    assert np.max(np.abs(avg - (-1j * np.cos(U * t / 2)))) < 1e-13
+
+
+def test_equilibrium_sum_rule_and_ph_symmetry():
+    cfg = W.config_c1()
+    Gg, Gl, _ = oracle.green_equilibrium(cfg["model"], [(0, 0), (1, 0), (3, 0)], 0.1, 30)
+    assert np.max(np.abs(1j * (Gg[0] - Gl[0]) - np.eye(3))) < 1e-12
+    # particle-hole symmetric star SIAM: G^R_imp(t) is purely imaginary
+    assert np.max(np.abs((Gg - Gl)[:, 0, 0].real)) < 1e-11
+    # ring without the -U/2 shift: e^{iUt/2} G^R_ii(t) is purely imaginary
+    U = 3.0
+    m = W.hubbard_ring(6, U, 3, 3)
+    Gg, Gl, _ = oracle.green_equilibrium(m, [(0, 0)], 0.1, 25)
+    t = 0.1 * np.arange(26)
+    assert np.max(np.abs((np.exp(1j * U * t / 2) * (Gg - Gl)[:, 0, 0]).real)) < 1e-11
+
+
+# ------------------------------------------------------------ Keldysh pins
+def test_keldysh_U0_quench_closed_form():
+    L = 6
+    ini = W.random_model(L, 3, 2, seed=8, complex_hopping=True)
+    fin = W.random_model(L, 3, 2, seed=9, complex_hopping=True)
+    ini["U"][:] = 0.0
+    fin["U"][:] = 0.0
+    eps_i, eps_f = ini["eps"], fin["eps"]
+    orbs = [(0, 0), (2, 0), (5, 0), (1, 1), (3, 1)]
+    dt, nt = 0.3, 7
+    Gl, Gg, _ = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    for spin, N in ((0, 3), (1, 2)):
+        w, v = np.linalg.eigh(ini["h"] + np.diag(eps_i[spin]))
+        assert w[N] - w[N - 1] > 1e-3
+        rho = v[:, :N] @ v[:, :N].conj().T   # rho[k, l] = <c^dag_l c_k>
+        hf = fin["h"] + np.diag(eps_f[spin])
+        idx = [k for k, o in enumerate(orbs) if o[1] == spin]
+        for k in range(nt):
+            Uk = sla.expm(-1j * hf * dt * k)
+            for l in range(nt):
+                Ul = sla.expm(-1j * hf * dt * l)
+                ref_l = 1j * Uk @ rho @ Ul.conj().T
+                ref_g = -1j * Uk @ (np.eye(L) - rho) @ Ul.conj().T
+                for a in idx:
+                    for b in idx:
+                        i, j = orbs[a][0], orbs[b][0]
+                        assert abs(Gl[k, l, a, b] - ref_l[i, j]) < 1e-12
+                        assert abs(Gg[k, l, a, b] - ref_g[i, j]) < 1e-12
+
+
+def test_keldysh_vs_dense_interacting():
+    L = 3
+    c = jw_parts(L)
+    ini = W.siam_chain(L, 2.0, 2, 1, field=0.4)
+    fin = W.siam_chain(L, 2.0, 2, 1, field=0.0)
+    orbs = [(0, 0), (1, 0), (2, 1)]
+    dt, nt = 0.4, 5
+    Gl, Gg, E0 = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    Hi, Hf = dense_fock_h(ini, c), dense_fock_h(fin, c)
+    i0 = sector_index(L, 2, 1)
+    w, v = np.linalg.eigh(Hi[np.ix_(i0, i0)])
+    g = np.zeros(Hi.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    Us = [sla.expm(-1j * Hf * dt * k) for k in range(nt)]
+
+    def heis(op, k):  # c(t_k) = U^dag op U
+        return Us[k].conj().T @ op @ Us[k]
+
+    for k in range(nt):
+        for l in range(nt):
+            for a, (ia, sa) in enumerate(orbs):
+                for b, (ib, sb) in enumerate(orbs):
+                    ca, cb = c[sa * L + ia], c[sb * L + ib]
+                    ref_l = 1j * (g.conj() @ heis(cb.T, l) @ heis(ca, k) @ g)
+                    ref_g = -1j * (g.conj() @ heis(ca, k) @ heis(cb.T, l) @ g)
+                    assert abs(Gl[k, l, a, b] - ref_l) < 1e-12
+                    assert abs(Gg[k, l, a, b] - ref_g) < 1e-12
+
+
+def test_keldysh_invariants_and_no_quench():
+    m_i = W.siam_chain(6, 2.0, 3, 3, field=0.3)
+    m_f = W.siam_chain(6, 2.0, 3, 3, field=0.0)
+    orbs = [(i, 0) for i in range(6)] + [(i, 1) for i in range(6)]
+    dt, nt = 0.25, 6
+    Gl, Gg, _ = oracle.green_keldysh(m_i, m_f, orbs, dt, nt)
+    n = len(orbs)
+    for k in range(nt):
+        # sum rule i (G^> - G^<)(t,t) = delta (Section 4, discussion of Fig. 2)
+        assert np.max(np.abs(1j * (Gg[k, k] - Gl[k, k]) - np.eye(n))) < 1e-12
+        # particle number: sum_i n_i,sigma(t) = N_sigma (n = -i G^<_ii(t,t))
+        occ = (-1j * np.diag(Gl[k, k])).real
+        assert abs(occ[:6].sum() - 3) < 1e-12 and abs(occ[6:].sum() - 3) < 1e-12
+    # hermiticity G^<_{ab}(t,t')^* = -G^<_{ba}(t',t), same for G^>
+    assert np.max(np.abs(Gl.conj() + Gl.transpose(1, 0, 3, 2))) < 1e-12
+    assert np.max(np.abs(Gg.conj() + Gg.transpose(1, 0, 3, 2))) < 1e-12
+    # no quench: G^<(t,t') equals the equilibrium hole part at t - t'
+    Gl0, _, _ = oracle.green_keldysh(m_f, m_f, [(0, 0), (2, 0)], dt, nt)
+    _, Gle, _ = oracle.green_equilibrium(m_f, [(0, 0), (2, 0)], dt, nt - 1)
+    for k in range(nt):
+        for l in range(k + 1):
+            assert np.max(np.abs(Gl0[k, l] - Gle[k - l])) < 1e-12
+
+
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_golden_fig2_equal_time_values():
+    g = _read_golden("fig2_siam_chain_t0.txt")
+    L, U = int(g["L"]), g["U"]
+    ini = W.siam_chain(L, U, int(g["n_up"]), int(g["n_dn"]), T=g["T"], field=g["field"])
+    fin = W.siam_chain(L, U, int(g["n_up"]), int(g["n_dn"]), T=g["T"], field=0.0)
+    les, gtr = oracle.keldysh_entry(ini, fin, (0, 0), (0, 0), 0.1, 0, 0)
+    assert abs(les.imag - gtr.imag - g["im_les_minus_im_gtr"]) < 1e-12
+    assert abs(les.real - g["re_les"]) < 1e-12 and abs(gtr.real - g["re_gtr"]) < 1e-12
+
+
+def test_golden_fig4_total_polarisation():
+    g = _read_golden("fig4_polarisation.txt")
+    L, U = int(g["L"]), g["U"]
+    ini = W.siam_chain(L, U, int(g["n_up"]), int(g["n_dn"]), T=g["T"], field=g["field"])
+    fin = W.siam_chain(L, U, int(g["n_up"]), int(g["n_dn"]), T=g["T"], field=0.0)
+    orbs = [(i, 0) for i in range(L)] + [(i, 1) for i in range(L)]
+    Gl, _, _ = oracle.green_keldysh(ini, fin, orbs, 1.0, 3)
+    for k in range(3):
+        n = (-1j * np.diag(Gl[k, k])).real
+        m = n[:L] - n[L:]
+        assert abs(m.sum() - g["sum_m"]) < 1e-11
+        assert abs(m[0]) > 1e-3  # the impurity is polarised at t = 0
