@@ -1,0 +1,386 @@
+"""Benchmark: Keldysh G(t,t') steps per second on the L = 12 Hubbard-ring quench.
+
+Workload (one GPU): the Hubbard ring L = 12, T = 1, PBC, half filling (6,6),
+d = 853,776; ground state at U = 8, quench to U = 4; dt = 0.05, Krylov M = 20,
+full reorthogonalisation, grid of 100 times, all 12 spin-up orbitals.
+A step is one row of step (iii) of the four-step method at the last grid time
+t_99 = 4.95: the c and c^dag maps of Phi(t_99) (24 columns in the N-1 and N+1
+sectors, d = 731,808 each), 99 backward Krylov steps per column
+(2 x 12 x 99 = 2376 G-steps) and the time-diagonal block G^<,>(t_99, t_99).
+Set-up (sector tables, ground state of H_ini, Phi(t_k) for all k) is not timed.
+
+Timed region: CUDA events on the library's launch stream, W >= 3 warm-up
+steps, K timed steps, barrier + synchronize on both sides, max over ranks.
+Every step streams its 2.9 GB Krylov basis and ~1.1 GB of other vectors, far
+beyond the 129 MB L2, so no flush is needed between steps.
+
+Under torchrun (N > 1) every rank runs the same kind of row on its own GPU
+(rank r takes row 99 - r); there is no collective on the data path (weak
+scaling).  `--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·ψ GB/s (frac. of HBM peak); G(t,t') steps/s, batched+adjoint vs plain GPU"
+UNIT = "G(t,t') steps/s"
+
+
+def shard_rows(n_t, world, rank):
+    """Rows of step (iii) owned by a rank: round robin from the costliest."""
+    return [k for k in range(n_t - 1, -1, -1) if (n_t - 1 - k) % world == rank]
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# Algorithmic bytes (read + write of complex FP64 vectors, 16 B per element)
+# of each kernel class over one propagation step of B columns of dimension d
+# with Krylov dimension M, full reorthogonalisation (one Gram-Schmidt pass).
+def step_bytes(d, B, M, n_ov=0):
+    v = 16.0 * d * B
+    hpsi = sum(v * (2 + (1 if j > 0 else 0)) for j in range(M))           # read V_j (+V_{j-1}), write W
+    dots = sum(v * (2 + (j + 1)) for j in range(M))                         # W, V_j, V_0..V_j
+    upd = sum(v * (3 + (j + 1)) for j in range(M))                          # W, V_j, V_0..V_j, write V_{j+1}
+    comb = v * (M + 1 + n_ov)
+    return {"lanczos_hpsi": hpsi, "reorth_dots": dots, "update": upd, "combine": comb, "colnorm": v}
+
+
+def step_flops(d, B, M, hops):
+    """FP64 operations (FMA = 2) per propagation step, by kernel class."""
+    e = float(d) * B
+    return {"lanczos_hpsi": sum(e * (2 * hops + 17) for _ in range(M)),
+            "reorth_dots": sum(e * (4 + 8 * (j + 1)) for j in range(M)),
+            "update": sum(e * (4 + 8 * (j + 1) + 4) for j in range(M)),
+            "combine": e * 8 * (M + 1), "colnorm": e * 4}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    cfg = W.config_c2()
+    n_t, dt, M = cfg["n_t"], cfg["dt"], cfg["M"]
+    orbs = cfg["orbitals"]
+    stream = torch.cuda.Stream()
+    opts = kg.kg_opts_default(M=M, reorth=1, stream=stream.cuda_stream)
+    t_setup = time.perf_counter()
+    si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+    E0, res, gap = si.ground_state(opts)
+    K = kg.Keldysh(si, sf, orbs, dt, n_t, opts)
+    t_setup = time.perf_counter() - t_setup
+    k_row = shard_rows(n_t, world, rank)[0]
+    d_nb = sf.neighbour_dim(0, False)
+    gsteps = 2 * len(orbs) * k_row  # (les, gtr) x orbitals x k backward steps
+
+    for _ in range(args.warmup):
+        K.row(k_row)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    gpu_index = local
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    n0 = kg.kg_launch_count()
+    with ClockSampler(gpu_index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            K.row(k_row)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = kg.kg_launch_count() - n0
+    t = e0.elapsed_time(e1) * 1e-3
+    t_max = t
+    total_gsteps = gsteps * args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        gg = torch.tensor([total_gsteps], dtype=torch.float64, device="cuda")
+        dist.all_reduce(gg, op=dist.ReduceOp.SUM)
+        total_gsteps = float(gg.item())
+    value = total_gsteps / t_max
+
+    # ---- end to end through the C ABI with host buffers: Phi(t_k) from pinned
+    # host memory in, the G(t_k, t_k) block back to host memory, every step.
+    phi_host = torch.empty(sf.dim, dtype=torch.complex128).pin_memory()
+    phi_host.numpy()[:] = K.get_phi(k_row)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ke = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(ke):
+        K.set_phi(k_row, phi_host.numpy())
+        K.row(k_row)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e2.elapsed_time(e3) * 1e-3
+    e2e = {"value": gsteps * ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 16 * sf.dim,
+           "d2h_bytes_per_step": 2 * 16 * len(orbs) ** 2}
+
+    # ---- roofline: per-kernel event timing of one profiled row
+    peaks, peak_kind = read_peaks()
+    fp64 = kg.kg_probe_fp64(stream)
+    k_prof = min(k_row, 10)
+    kg.kg_profile_start()
+    K.row(k_prof)
+    prof = kg.kg_profile_stop()
+    n_prof_steps = 2 * k_prof  # propagation steps (each of 12 columns) in the profiled row
+    # mean allowed ring hops per state of the (5,6) column sector: 2L bonds x
+    # P(site occupied, neighbour empty) summed over both spins
+    L_, nu_, nd_ = 12, 5, 6
+    hops = 2.0 * L_ * (nu_ * (L_ - nu_) + nd_ * (L_ - nd_)) / (L_ * (L_ - 1))
+    by = step_bytes(d_nb, len(orbs), M)
+    fl = step_flops(d_nb, len(orbs), M, hops)
+    kernels = {}
+    tot_ms = sum(ms for _, ms in prof.values()) or 1.0
+    for name, (n, ms) in prof.items():
+        ent = {"launches": n, "ms": round(ms, 3), "share": round(ms / tot_ms, 4)}
+        if name in by:
+            ent["gbs"] = round(by[name] * n_prof_steps / (ms * 1e-3) / 1e9, 1)
+            ent["tflops_fp64"] = round(fl[name] * n_prof_steps / (ms * 1e-3) / 1e12, 3)
+        kernels[name] = ent
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dom]
+    hbm_frac = dk.get("gbs", 0.0) / peaks["hbm_gbs"]
+    fp_frac = dk.get("tflops_fp64", 0.0) / fp64
+    traffic = None
+    tj = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tj):
+        rec = json.load(open(tj)).get(dom)
+        if rec and rec.get("source_hash") == source_hash(rec.get("sources", [])):
+            traffic = rec.get("bytes_per_launch")
+    if hbm_frac >= fp_frac:
+        roof = {"bound": "hbm", "achieved": dk.get("gbs"), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": dom,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": dk.get("tflops_fp64"), "peak": round(fp64, 3), "unit": "TFLOP/s",
+                "frac": round(fp_frac, 4), "traffic": traffic, "kernel": dom,
+                "peak_source": "FP64 FMA throughput measured live by kg_probe_fp64"}
+
+    # ---- H*psi alone (the metric's first half), buffers rotated beyond L2
+    nbuf = 12
+    xs = [torch.randn(d_nb, dtype=torch.complex128, device="cuda") for _ in range(nbuf)]
+    ys = [torch.empty_like(x) for x in xs]
+    nb_sec = kg.Sector(W.with_sector(cfg["fin"], 5, 6))
+    with torch.cuda.stream(stream):
+        for i in range(nbuf):
+            nb_sec.hpsi(xs[i], ys[i], stream)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        h0.record(stream)
+        for _ in range(reps):
+            for i in range(nbuf):
+                nb_sec.hpsi(xs[i], ys[i], stream)
+        h1.record(stream)
+        torch.cuda.synchronize()
+    t_h = h0.elapsed_time(h1) * 1e-3 / (reps * nbuf)
+    hpsi = {"d": d_nb, "us": round(t_h * 1e6, 2), "gbs": round(32.0 * d_nb / t_h / 1e9, 1),
+            "frac_hbm": round(32.0 * d_nb / t_h / 1e9 / peaks["hbm_gbs"], 4),
+            "algorithmic_bytes": 32 * d_nb, "l2": "12 rotating x/y pairs, 281 MB > L2"}
+
+    # ---- CPU baseline: the oracle on the host cores, a bounded sample
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args.cpu_seconds)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c2 Hubbard ring L=12 (6,6) d=853776, U=8 -> U=4 quench; Keldysh step (iii) "
+                                   "row t_%d: 24 columns x %d G-steps (dt=0.05, M=20, full reorth) + "
+                                   "G(t_k,t_k) block" % (k_row, k_row),
+                       "global_batch_gsteps_per_step": gsteps * world, "columns": 2 * len(orbs),
+                       "sector_dim": sf.dim, "column_dim": d_nb, "M": M, "reorth": 1,
+                       "l2": "inputs larger than L2 (2.9 GB Krylov basis per step)",
+                       "parallelism": "rows sharded over %d rank(s), no data-path collective" % world},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "hpsi": hpsi,
+            "fp64_tflops_measured": round(fp64, 3), "cpu_baseline": cpu, "clocks": clocks,
+            "setup_s": round(t_setup, 2), "E0_ini": E0, "gs_resid": res,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(budget_s):
+    """Oracle G-steps (exp(-iH dt) on one column of the N-1 sector) timed on the
+    host cores until about budget_s seconds of work are done."""
+    import oracle
+    import workloads as W
+    cfg = W.config_c2()
+    sec = oracle.Sector(W.with_sector(cfg["fin"], 5, 6))
+    x = W.random_state(sec.dim, 99)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        x = sec.propagate(x, -cfg["dt"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 200:
+            break
+    return {"value": round(n / el, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d oracle G-steps (Chebyshev exp(+iH*0.05) of one c2 N-1 column, d=%d) in %.1f s"
+                      % (n, sec.dim, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    cfg = W.config_c2()
+    sec = oracle.Sector(W.with_sector(cfg["fin"], 5, 6))
+    x = W.random_state(sec.dim, 99)
+    per_step = max(1, args.ref_gsteps)
+    for _ in range(args.warmup):
+        x = sec.propagate(x, -cfg["dt"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            x = sec.propagate(x, -cfg["dt"])
+    el = time.perf_counter() - t0
+    value = args.steps * per_step / el
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c2 Keldysh step (iii) G-steps on the CPU oracle (bounded sample of the c2 row)",
+                   "column_dim": sec.dim, "gsteps_per_step": per_step},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d oracle G-steps per step on one c2 N-1 column" % per_step},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-gsteps", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

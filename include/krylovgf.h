@@ -1,0 +1,219 @@
+/*
+ * krylovgf.h -- C ABI of libkrylovgf, a GB300 (sm_103a) implementation of the
+ * Krylov-space method for the zero-temperature single-particle Green's
+ * function of Balzer, Gdaniec and Potthoff ("Krylov-space approach to the
+ * equilibrium and the nonequilibrium single-particle Green's function").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Model (Sections 3 and 4 of the paper, written for one spin-conserving
+ * hopping matrix):
+ *     H = sum_sigma sum_{i != j} h_ij c^dag_{i sigma} c_{j sigma}
+ *         + sum_{i sigma} (eps_{i sigma} + h_ii) n_{i sigma}
+ *         + sum_i U_i n_{i up} n_{i dn}
+ * The paper writes the hopping as -T sum c^dag c, so callers pass h_ij = -T.
+ * A local field H_field = -h (n_up - n_dn) (Eq. (hfi)) is passed through eps.
+ *
+ * Sector and basis (Section 2: H_jj' in the occupation-number basis; Section 4:
+ * particle number and S_z as good quantum numbers): a sector is (L, N_up,
+ * N_dn) with D_up = C(L, N_up) up strings and D_dn = C(L, N_dn) down strings.
+ * A spin string's index is its rank in ascending numeric order among the
+ * L-bit words with that popcount (the combinatorial number system).  The
+ * state index is  s = i_dn * D_up + i_up  (i_up fastest), dimension
+ * d = D_up * D_dn.  Fermion order: all up orbitals (site order), then all
+ * down orbitals; c^dag_{i sigma} carries the sign (-1)^(number of occupied
+ * orbitals before (i, sigma)).
+ *
+ * Vectors are complex FP64, interleaved (re, im): a vector of dimension d is
+ * 2*d doubles.  "_dev" pointers are device memory of the current CUDA device,
+ * "_host" pointers host memory; the caller owns both.  The library owns every
+ * buffer it allocates behind a handle, until the handle is freed.
+ *
+ * Orbitals are passed as n_orb pairs orb[2a] = site, orb[2a+1] = spin (0 up,
+ * 1 down).  Green's functions are complex FP64 arrays (interleaved) with the
+ * orbital pair innermost: G[...][a][a'] = G_{a a'}.
+ *
+ * Every call returns KG_OK (0) or a negative status; no exception and no
+ * abort crosses this boundary.  kg_last_error() gives a message for the most
+ * recent failure on the calling thread.  One handle must not be used by two
+ * threads at once.  Calls are stream-ordered on opts->stream (or the
+ * sector's own stream when it is NULL) and return after the results they
+ * write to host memory are complete.
+ */
+#ifndef KRYLOVGF_H
+#define KRYLOVGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KG_OK          0
+#define KG_EINVAL     (-1)  /* bad argument, bad sector pair, bad call order   */
+#define KG_ENOMEM     (-2)  /* device or host allocation failed / too large    */
+#define KG_ENOCONV    (-3)  /* ground state not converged in max_restarts      */
+#define KG_EDEGEN     (-4)  /* ground state (near) degenerate: gap < 1e-8      */
+#define KG_EBREAKDOWN (-5)  /* informational: Krylov space became invariant    */
+#define KG_ENUMERIC   (-6)  /* NaN or Inf met in a norm or dot product         */
+#define KG_ETIMEOUT   (-7)  /* a bounded device wait ran out                   */
+#define KG_ECUDA      (-8)  /* a CUDA runtime call failed                      */
+
+typedef struct kg_sector kg_sector;
+typedef struct kg_keldysh kg_keldysh;
+
+/* Solver options.  kg_opts_default() fills the defaults shown. */
+typedef struct kg_opts {
+    int M;              /* Krylov dimension n per propagation step, 1..64 (20)  */
+    int M_gs;           /* Krylov dimension per ground-state restart, 2..256 (100) */
+    int max_restarts;   /* ground-state restarts (200)                         */
+    double tol_resid;   /* ground state: stop when ||H0 - E0 0|| <=
+                           tol_resid * max(1, |E0|) (1e-12)                    */
+    int reorth;         /* 0: three-term recurrence only; 1: plus one full
+                           Gram-Schmidt pass against every stored Lanczos
+                           vector; 2: plus two passes (1)                       */
+    int batch;          /* columns per batched propagation launch, 0 = all (0) */
+    int schedule;       /* H*psi schedule; 0 = autotuned (0)                    */
+    int use_graphs;     /* replay each propagation step as a CUDA graph (1)    */
+    double dt_internal; /* Keldysh: Krylov step inside one grid step; 0 = dt   */
+    unsigned long long seed; /* ground-state start vector seed (1234)         */
+    void* stream;       /* cudaStream_t for all work; NULL = the sector's own
+                           stream, ordered after work already queued on the
+                           legacy default stream                               */
+} kg_opts;
+
+void kg_opts_default(kg_opts* o);
+
+/* ---- a1: sector basis and ranking ------------------------------------------
+ * Builds the (L, n_up, n_dn) sector of H (Section 2, occupation-number basis
+ * with N and S_z conserved) on the device: the spin strings by unranking in
+ * the combinatorial number system, the per-spin hop tables (source rank and
+ * fermion sign of every allowed c^dag_a c_b), the single-spin diagonal
+ * energies and the U table.
+ *   h_re, h_im : L*L row-major host arrays, h[i*L+j] = h_ij, Hermitian;
+ *                h_im may be NULL (real hopping).
+ *   eps        : 2*L host array, eps[sigma*L + i].
+ *   U          : L host array.
+ * Limits: 1 <= L <= 32, 0 <= n_up, n_dn <= L, d < 2^31.  Returns KG_EINVAL
+ * for bad sizes or non-Hermitian h, KG_ENOMEM when the tables do not fit.
+ * *out receives a handle that owns all device memory; free with
+ * kg_free_sector (which also frees the neighbour sectors it built). */
+int kg_build_sector(int L, int n_up, int n_dn, const double* h_re, const double* h_im,
+                    const double* eps, const double* U, kg_sector** out);
+void kg_free_sector(kg_sector* s);
+
+/* Dimensions of the sector (any pointer may be NULL). */
+int kg_sector_dims(const kg_sector* s, long long* dim, long long* D_up, long long* D_dn);
+
+/* Copies the unranked spin strings (bit i = site i occupied) to host arrays
+ * of D_up and D_dn entries: the device result of the combinatorial unranking. */
+int kg_sector_strings(const kg_sector* s, unsigned int* up_host, unsigned int* dn_host);
+
+/* ---- a2: H*psi --------------------------------------------------------------
+ * y = H x on the device (Section 2, the matrix H_jj' applied on the fly:
+ * hopping by bit flips with popcount fermion signs, diagonal eps and U).
+ * x_dev, y_dev: complex vectors of dimension d, must not overlap.
+ * stream: cudaStream_t; NULL means CUDA's legacy default stream.
+ * Asynchronous (stream-ordered). */
+int kg_hpsi(kg_sector* s, const double* x_dev, double* y_dev, void* stream);
+
+/* ---- a6: c / c^dag sector maps ------------------------------------------
+ * y = c_{site,spin} x (dagger = 0) or y = c^dag_{site,spin} x (dagger = 1),
+ * mapping sector (N_up, N_dn) to the neighbouring sector with N_spin -/+ 1
+ * (Section 3, the state c^dag_a' |0> of Eq. (psit); Section 4, step (iii)).
+ * x_dev has the dimension of s, y_dev that of the neighbour sector (query it
+ * with kg_neighbour_dim).  Returns KG_EINVAL if the neighbour does not exist
+ * (N_spin would leave [0, L]).  stream as for kg_hpsi.  Asynchronous. */
+int kg_neighbour_dim(kg_sector* s, int spin, int dagger, long long* dim);
+int kg_apply_cop(kg_sector* s, int site, int spin, int dagger, const double* x_dev, double* y_dev,
+                 void* stream);
+
+/* ---- a3-a5: ground state -------------------------------------------------
+ * Lanczos ground state of the sector (Section 2: recursion Eq. (recursion)
+ * with full reorthogonalisation, T of Eq. (tmatrix) diagonalised on the
+ * device, Eq. (tdiag), Ritz vector Eq. (eigen)), restarted from the Ritz
+ * vector until ||H|0> - E0|0>|| <= tol_resid*max(1,|E0|).  The ground state
+ * stays cached in the handle for the Green's-function calls.
+ * E0, resid, gap: host outputs (gap = second-lowest minus lowest Ritz value
+ * of the last restart, an estimate; any may be NULL).
+ * Returns KG_ENOCONV after max_restarts, KG_EDEGEN when gap < 1e-8. */
+int kg_ground_state(kg_sector* s, const kg_opts* o, double* E0, double* resid, double* gap);
+
+/* Copies the cached ground state (complex, dimension d) to psi; to_host != 0
+ * means psi is host memory, else device memory.  KG_EINVAL before
+ * kg_ground_state. */
+int kg_copy_ground_state(kg_sector* s, double* psi, int to_host);
+
+/* ---- a3-a5: Krylov propagation ------------------------------------------
+ * x <- exp(-i H dt)^n_steps x in place on the device (Section 3, Eqs.
+ * (newstate) and (udelta): one Lanczos space of dimension opts->M per step,
+ * T diagonalised on the device, exp(-i D dt) applied in the small space,
+ * the new state formed as V Q e^{-iD dt} Q^T e_1 ||x||).  dt < 0 propagates
+ * backward, exp(+i H |dt|).  Returns when x_dev holds the result. */
+int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_opts* o);
+
+/* ---- a7 + driver: equilibrium Green's function ---------------------------
+ * Section 3, Eqs. (psit)/(psigreen) with eta = 0, and the hole part given
+ * after Eq. (gomega); for t_k = k*dt, k = 0..n_steps:
+ *   G_gtr[k][a][a'] = -i e^{+i E0 t_k} <c^dag_a 0| e^{-iH t_k} |c^dag_a' 0>
+ *   G_les[k][a][a'] = +i e^{-i E0 t_k} <c_a' 0| e^{+iH t_k} |c_a 0>
+ * (the retarded G is G_gtr - G_les).  Runs kg_ground_state first if needed.
+ * G_gtr, G_les: host, complex [(n_steps+1)][n_orb][n_orb].  Entries of
+ * opposite spins are zero. */
+int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps,
+                         const kg_opts* o, double* G_gtr, double* G_les);
+
+/* ---- a8: nonequilibrium (Keldysh) Green's function -----------------------
+ * Section 4, steps (i)-(iv): |0> = ground state of H_ini; Phi(t) =
+ * e^{-iH t}|0> with H = H_fin; Psi_a(t) = e^{iHt} c_a Phi(t) and
+ * chi_a(t) = e^{iHt} c^dag_a Phi(t); then for t_k = k*dt, k < n_t,
+ *   G_les[k][l][a][a'] = +i <Psi_a'(t_l) | Psi_a(t_k)>
+ *   G_gtr[k][l][a][a'] = -i <chi_a(t_k) | chi_a'(t_l)>.
+ * H_ini and H_fin must have the same (L, N_up, N_dn), else KG_EINVAL.
+ * opts->dt_internal splits every grid step into round(dt/dt_internal)
+ * Krylov steps.  G_les, G_gtr: host, complex [n_t][n_t][n_orb][n_orb]. */
+int kg_green_keldysh(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt,
+                     int n_t, const kg_opts* o, double* G_les, double* G_gtr);
+
+/* The same computation in stages, so that a caller can schedule the rows of
+ * step (iii) itself.  kg_keldysh_create runs steps (i) and (ii) and keeps
+ * Phi(t_k) for all k on the device.  kg_keldysh_row runs step (iii) for one
+ * time index k -- every Psi_a(t_k) and chi_a(t_k) of the orbital list,
+ * batched -- stores them, and writes the time-diagonal block G(t_k, t_k)
+ * (host, complex [n_orb][n_orb] each; either pointer may be NULL).
+ * kg_keldysh_gram runs step (iv) over all stored rows (rows never computed
+ * give KG_EINVAL) into arrays shaped like kg_green_keldysh's. */
+int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt,
+                      int n_t, const kg_opts* o, kg_keldysh** out);
+int kg_keldysh_row(kg_keldysh* K, int k, double* G_les_kk, double* G_gtr_kk);
+int kg_keldysh_gram(kg_keldysh* K, double* G_les, double* G_gtr);
+/* Host copy of Phi(t_k) (complex, dimension d), and the reverse: replaces
+ * the stored Phi(t_k) by a host vector (used to time a row end to end). */
+int kg_keldysh_get_phi(kg_keldysh* K, int k, double* phi_host);
+int kg_keldysh_set_phi(kg_keldysh* K, int k, const double* phi_host);
+void kg_keldysh_free(kg_keldysh* K);
+
+/* ---- measurement (not part of the method) ---------------------------------
+ * kg_profile_start/stop bracket a region in which every kernel launch of
+ * this library is timed with CUDA events on its launch stream (CUDA graphs
+ * are not used while profiling).  After stop, kg_profile_count entries are
+ * available: kernel name (copied into name[len]), number of launches and
+ * total milliseconds.  kg_probe_fp64 runs a dependent-FMA-free FP64 kernel on
+ * the current device and reports the FMA throughput in TFLOP/s (2 flops per
+ * FMA); stream as for kg_hpsi. */
+int kg_profile_start(void);
+int kg_profile_stop(void);
+int kg_profile_count(void);
+int kg_profile_get(int i, char* name, int len, long long* launches, double* ms);
+int kg_probe_fp64(double* tflops, void* stream);
+
+/* ---- utilities ----------------------------------------------------------- */
+const char* kg_strerror(int code);
+const char* kg_last_error(void);
+
+/* Number of kernel launches this library has issued since load (graph
+ * replays count their kernels); a counter for benchmark bookkeeping. */
+unsigned long long kg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRYLOVGF_H */

@@ -144,16 +144,39 @@ static void gershgorin(ko_model* M) {
     M->hi = hi;
 }
 
+// Dot products and norms: each thread sums one fixed contiguous slice, the
+// slice sums are added in slice order, so the result does not depend on
+// timing (only on the thread count).
 static cd vdot(const cd* a, const cd* b, long n) {
+#ifdef _OPENMP
+    const int nt = omp_get_max_threads();
+#else
+    const int nt = 1;
+#endif
+    std::vector<cd> part(nt, cd(0.0, 0.0));
+#pragma omp parallel num_threads(nt)
+    {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num();
+#else
+        const int t = 0;
+#endif
+        const long lo = n * t / nt, hi = n * (t + 1) / nt;
+        cd s(0.0, 0.0);
+        for (long i = lo; i < hi; ++i) s += std::conj(a[i]) * b[i];
+        part[t] = s;
+    }
     cd s(0.0, 0.0);
-    for (long i = 0; i < n; ++i) s += std::conj(a[i]) * b[i];
+    for (const cd& p : part) s += p;
     return s;
 }
 
-static double vnorm(const cd* a, long n) {
-    double s = 0.0;
-    for (long i = 0; i < n; ++i) s += std::norm(a[i]);
-    return std::sqrt(s);
+static double vnorm(const cd* a, long n) { return std::sqrt(vdot(a, a, n).real()); }
+
+// y -= c * x
+static void vaxpy(cd c, const cd* x, cd* y, long n) {
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) y[i] -= c * x[i];
 }
 
 // Cyclic Jacobi eigenvalue algorithm for a dense real symmetric matrix
@@ -302,19 +325,16 @@ int ko_ground_state(const ko_model* M, int K, int max_restarts, double tol, unsi
         for (int j = 0; j < kmax; ++j) {
             hpsi_impl(M, V[j].data(), w.data());
             const double a = vdot(V[j].data(), w.data(), d).real();
-            for (long i = 0; i < d; ++i) w[i] -= a * V[j][i];
-            if (j > 0)
-                for (long i = 0; i < d; ++i) w[i] -= beta[j] * V[j - 1][i];
+            vaxpy(a, V[j].data(), w.data(), d);
+            if (j > 0) vaxpy(beta[j], V[j - 1].data(), w.data(), d);
             for (int pass = 0; pass < 2; ++pass)
-                for (int k = 0; k <= j; ++k) {
-                    const cd c = vdot(V[k].data(), w.data(), d);
-                    for (long i = 0; i < d; ++i) w[i] -= c * V[k][i];
-                }
+                for (int k = 0; k <= j; ++k) vaxpy(vdot(V[k].data(), w.data(), d), V[k].data(), w.data(), d);
             alpha.push_back(a);
             const double b = vnorm(w.data(), d);
             if (j + 1 == kmax || b <= 1e-13 * (std::fabs(a) + beta[j] + 1e-300)) break;
             beta.push_back(b);
             std::vector<cd> nv(d);
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < d; ++i) nv[i] = w[i] / b;
             V.push_back(nv);
         }
@@ -327,8 +347,7 @@ int ko_ground_state(const ko_model* M, int K, int max_restarts, double tol, unsi
         for (int i = 1; i < m; ++i)
             if (ev[i] < ev[i0]) i0 = i;
         for (long i = 0; i < d; ++i) u[i] = 0.0;
-        for (int k = 0; k < m; ++k)
-            for (long i = 0; i < d; ++i) u[i] += Z[(size_t)k * m + i0] * V[k][i];
+        for (int k = 0; k < m; ++k) vaxpy(-Z[(size_t)k * m + i0], V[k].data(), u.data(), d);
         const double nu_ = vnorm(u.data(), d);
         for (auto& z : u) z /= nu_;
         hpsi_impl(M, u.data(), Hu.data());
@@ -369,11 +388,14 @@ int ko_propagate(const ko_model* M, const double* x_, double tau, double* y_) {
     while (true) {
         ++k;
         hpsi_impl(M, t1.data(), tmp.data());
-        for (long i = 0; i < d; ++i) t2[i] = 2.0 * (tmp[i] - b * t1[i]) / a - t0[i];
         ph *= step;
         const double jk = std::cyl_bessel_j((double)k, az);
         const cd ck = 2.0 * ph * jk;
-        for (long i = 0; i < d; ++i) y[i] += ck * t2[i];
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < d; ++i) {
+            t2[i] = 2.0 * (tmp[i] - b * t1[i]) / a - t0[i];
+            y[i] += ck * t2[i];
+        }
         std::swap(t0, t1);
         std::swap(t1, t2);
         if (k > az && std::fabs(jk) < 1e-18) {

@@ -1,0 +1,614 @@
+// kg_green.cu -- a7/a8: the Green's-function drivers.
+//
+// Equilibrium (Section 3, Eqs. (psit), (psigreen), eta = 0; hole part after
+// Eq. (gomega)):  the columns c^dag_a'|0> (particle) and c_a|0> (hole) are
+// propagated together, one batched Krylov step per time step, and their
+// overlaps with the fixed vectors c^dag_a|0> / c_a'|0> are fused into the
+// combination pass of every step.
+//
+// Nonequilibrium (Section 4, steps (i)-(iv)): Phi(t_k) = e^{-iHt_k}|0> is
+// stored for every grid time; row k of step (iii) starts the columns
+// c_a Phi(t_k) (or c^dag_a Phi(t_k)) and propagates them backward by t_k;
+// step (iv) is a Hermitian Gram matrix over all stored columns.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "kg_internal.h"
+
+namespace kg {
+
+int launch_overlaps_cs(Krylov& K, const double2* x, size_t x_stride, const double2* ov, int n_ov,
+                       size_t ov_stride, double2* ov_out, int ov_rows, cudaStream_t st);
+
+// Replays the launch sequence of one propagation step, as a CUDA graph when
+// allowed (the sequence is fixed: iteration counts and early exits after a
+// breakdown are decided on the device).
+struct StepRunner {
+    StepPlan plan;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    bool graph = false;
+
+    int init(const StepPlan& P, cudaStream_t st, bool use_graph) {
+        plan = P;
+        graph = false;
+        if (!use_graph || profiling()) return KG_OK;
+        cudaGraph_t g = nullptr;
+        KG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
+        const int rc = enqueue_step(P, st);
+        set_capturing(false);
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != KG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        cudaGraphGetNodes(g, nullptr, &nodes);
+        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+        graph = true;
+        return KG_OK;
+    }
+    int run(cudaStream_t st) {
+        if (!graph || profiling()) return enqueue_step(plan, st);
+        KG_CUDA(cudaGraphLaunch(exec, st));
+        count_launch(nodes);
+        return KG_OK;
+    }
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        graph = false;
+    }
+};
+
+static int reset_slots(Krylov& K, cudaStream_t st) {
+    // ov_slot of every column back to 0 (one int per ColScalars record)
+    KG_CUDA(cudaMemset2DAsync(&K.cs->ov_slot, sizeof(ColScalars), 0, sizeof(int), K.B, st));
+    return KG_OK;
+}
+
+static int ensure_gs(kg_sector* s, const kg_opts* o) {
+    if (s->has_gs) return KG_OK;
+    return ground_state(s, o);
+}
+
+static void groups(const int* orb, int n_orb, std::vector<int> idx[2]) {
+    idx[0].clear();
+    idx[1].clear();
+    for (int a = 0; a < n_orb; ++a) idx[orb[2 * a + 1]].push_back(a);
+}
+
+static int check_orbitals(const kg_sector* s, const int* orb, int n_orb) {
+    if (!orb || n_orb < 1) {
+        set_error("empty orbital list");
+        return KG_EINVAL;
+    }
+    for (int a = 0; a < n_orb; ++a)
+        if (orb[2 * a] < 0 || orb[2 * a] >= s->L || (orb[2 * a + 1] != 0 && orb[2 * a + 1] != 1)) {
+            set_error("orbital %d = (%d,%d) out of range", a, orb[2 * a], orb[2 * a + 1]);
+            return KG_EINVAL;
+        }
+    std::vector<int> idx[2];
+    groups(orb, n_orb, idx);
+    if ((int)idx[0].size() > kMaxOv || (int)idx[1].size() > kMaxOv) {
+        set_error("at most %d orbitals per spin", kMaxOv);
+        return KG_EINVAL;
+    }
+    return KG_OK;
+}
+
+static int check_opts(const kg_opts* o) {
+    if (o->M < 1 || o->M > kMaxM) {
+        set_error("M must be in [1, %d]", kMaxM);
+        return KG_EINVAL;
+    }
+    if (o->reorth < 0 || o->reorth > 2) {
+        set_error("reorth must be 0, 1 or 2");
+        return KG_EINVAL;
+    }
+    return KG_OK;
+}
+
+// ------------------------------------------------------------ equilibrium
+int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
+                      double* G_gtr, double* G_les) {
+    KG_TRY(check_orbitals(s, orb, n_orb));
+    KG_TRY(check_opts(o));
+    if (n_steps < 0 || !G_gtr || !G_les) {
+        set_error("bad n_steps or NULL output");
+        return KG_EINVAL;
+    }
+    KG_TRY(ensure_gs(s, o));
+    cudaStream_t st = pick_stream(s, o);
+    const size_t per_t = (size_t)n_orb * n_orb * 2;
+    std::memset(G_gtr, 0, sizeof(double) * per_t * (n_steps + 1));
+    std::memset(G_les, 0, sizeof(double) * per_t * (n_steps + 1));
+    std::vector<int> idx[2];
+    groups(orb, n_orb, idx);
+    const int rows = n_steps + 1;
+    for (int spin = 0; spin < 2; ++spin) {
+        const int na = (int)idx[spin].size();
+        if (!na) continue;
+        for (int dagger = 1; dagger >= 0; --dagger) {
+            kg_sector* nb = nullptr;
+            if (neighbour(s, spin, dagger, &nb) != KG_OK) continue;  // empty/full: G part is zero
+            const int dn = (int)nb->d;
+            Krylov K;
+            double2 *chi = nullptr, *ov = nullptr;
+            StepRunner R;
+            int rc = krylov_alloc(K, na, std::min(o->M, dn), dn, s->nsm);
+            if (rc == KG_OK && cudaMalloc(&chi, sizeof(double2) * (size_t)na * dn) != cudaSuccess) rc = KG_ENOMEM;
+            if (rc == KG_OK && cudaMalloc(&ov, sizeof(double2) * (size_t)na * rows * na) != cudaSuccess) rc = KG_ENOMEM;
+            for (int a = 0; rc == KG_OK && a < na; ++a)
+                rc = launch_cop(s, nb, orb[2 * idx[spin][a]], spin, dagger, s->gs, chi + (size_t)a * dn, st);
+            if (rc == KG_OK)
+                rc = cudaMemcpy2DAsync(K.V, K.colV() * sizeof(double2), chi, (size_t)dn * sizeof(double2),
+                                       (size_t)dn * sizeof(double2), na, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                         ? KG_OK
+                         : KG_ECUDA;
+            if (rc == KG_OK) rc = reset_slots(K, st);
+            if (rc == KG_OK) rc = launch_overlaps_cs(K, K.V, K.colV(), chi, na, dn, ov, rows, st);
+            StepPlan P;
+            P.sec = nb;
+            P.K = &K;
+            P.reorth = o->reorth;
+            P.tau = dagger ? dt : -dt;  // particle: e^{-iHt}; hole: e^{+iHt}
+            P.ov = chi;
+            P.n_ov = na;
+            P.ov_stride = dn;
+            P.ov_out = ov;
+            P.ov_rows = rows;
+            if (rc == KG_OK && n_steps > 0) rc = R.init(P, st, o->use_graphs != 0);
+            for (int k = 1; rc == KG_OK && k <= n_steps; ++k) rc = R.run(st);
+            std::vector<double2> hov((size_t)na * rows * na);
+            if (rc == KG_OK &&
+                (cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * hov.size(), cudaMemcpyDeviceToHost, st) !=
+                     cudaSuccess ||
+                 cudaStreamSynchronize(st) != cudaSuccess))
+                rc = cuda_fail(cudaGetLastError(), "overlap readback", __FILE__, __LINE__);
+            int status = KG_OK;
+            if (rc == KG_OK) {
+                std::vector<ColScalars> hcs(na);
+                cudaMemcpy(hcs.data(), K.cs, sizeof(ColScalars) * na, cudaMemcpyDeviceToHost);
+                for (auto& c : hcs)
+                    if (c.status == KG_ENUMERIC) status = KG_ENUMERIC;
+            }
+            R.release();
+            krylov_free(K);
+            cudaFree(chi);
+            cudaFree(ov);
+            if (rc != KG_OK) return rc;
+            if (status != KG_OK) {
+                set_error("non-finite value during propagation");
+                return status;
+            }
+            // assemble: ov[b][k][a] = <vec_a | propagated vec_b at t_k>
+            for (int k = 0; k < rows; ++k) {
+                const double t = dt * k;
+                const std::complex<double> ph = dagger ? std::complex<double>(0.0, -1.0) * std::exp(std::complex<double>(0.0, s->E0 * t))
+                                                       : std::complex<double>(0.0, 1.0) * std::exp(std::complex<double>(0.0, -s->E0 * t));
+                for (int bcol = 0; bcol < na; ++bcol)
+                    for (int a = 0; a < na; ++a) {
+                        const double2 v = hov[((size_t)bcol * rows + k) * na + a];
+                        const std::complex<double> g = ph * std::complex<double>(v.x, v.y);
+                        // particle: G^>_{a, b}; hole: G^<_{b, a}
+                        const int r = dagger ? idx[spin][a] : idx[spin][bcol];
+                        const int c = dagger ? idx[spin][bcol] : idx[spin][a];
+                        double* G = dagger ? G_gtr : G_les;
+                        G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2] = g.real();
+                        G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2 + 1] = g.imag();
+                    }
+            }
+        }
+    }
+    return KG_OK;
+}
+
+// --------------------------------------------------- a7: Gram, step (iv)
+// G[p][q] = <X_p | X_q> for the upper-triangle tiles (p tile <= q tile) of a
+// set of nv vectors of dimension d, FP64 on the CUDA cores.  32 x 32 output
+// tile per block, 2 x 2 complex outputs per thread, 16-element slabs of the
+// vectors staged in shared memory, split over d by gridDim.z (partials).
+constexpr int kGT = 32, kGK = 16;
+
+__global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ X, int nv, int d, int ntile,
+                                              const int2* __restrict__ tiles, double2* __restrict__ part) {
+    __shared__ double2 As[kGT][kGK + 1];
+    __shared__ double2 Bs[kGK][kGT + 1];
+    const int2 tl = tiles[blockIdx.x];
+    const int p0 = tl.x * kGT, q0 = tl.y * kGT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int z = blockIdx.y, nz = gridDim.y;
+    const int slab = (d + nz - 1) / nz;
+    const int i_begin = z * slab, i_end = min(d, i_begin + slab);
+    double2 acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+    for (int i0 = i_begin; i0 < i_end; i0 += kGK) {
+        // 32 rows x 16 elements of each operand: 2 loads per thread
+        for (int t = threadIdx.x; t < kGT * kGK; t += 256) {
+            const int r = t / kGK, c = t % kGK;
+            const int i = i0 + c;
+            const int p = p0 + r, q = q0 + r;
+            As[r][c] = (p < nv && i < i_end) ? X[(size_t)p * d + i] : make_double2(0.0, 0.0);
+            Bs[c][r] = (q < nv && i < i_end) ? X[(size_t)q * d + i] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kGK; ++c) {
+            const double2 a0 = As[ty][c], a1 = As[ty + 16][c];
+            const double2 b0 = Bs[c][tx], b1 = Bs[c][tx + 16];
+            acc[0][0].x = fma(a0.x, b0.x, fma(a0.y, b0.y, acc[0][0].x));
+            acc[0][0].y = fma(a0.x, b0.y, fma(-a0.y, b0.x, acc[0][0].y));
+            acc[0][1].x = fma(a0.x, b1.x, fma(a0.y, b1.y, acc[0][1].x));
+            acc[0][1].y = fma(a0.x, b1.y, fma(-a0.y, b1.x, acc[0][1].y));
+            acc[1][0].x = fma(a1.x, b0.x, fma(a1.y, b0.y, acc[1][0].x));
+            acc[1][0].y = fma(a1.x, b0.y, fma(-a1.y, b0.x, acc[1][0].y));
+            acc[1][1].x = fma(a1.x, b1.x, fma(a1.y, b1.y, acc[1][1].x));
+            acc[1][1].y = fma(a1.x, b1.y, fma(-a1.y, b1.x, acc[1][1].y));
+        }
+        __syncthreads();
+    }
+    double2* out = part + (size_t)z * ntile * kGT * kGT + (size_t)blockIdx.x * kGT * kGT;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) out[(ty + 16 * a) * kGT + tx + 16 * b] = acc[a][b];
+}
+
+__global__ void k_gram_reduce(const double2* part, int nz, int ntile, const int2* tiles, int nv, double2* G) {
+    const int t = blockIdx.x, e = threadIdx.x + blockDim.x * blockIdx.y;
+    if (e >= kGT * kGT) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int z = 0; z < nz; ++z) {
+        const double2 v = part[((size_t)z * ntile + t) * kGT * kGT + e];
+        s.x += v.x;
+        s.y += v.y;
+    }
+    const int2 tl = tiles[t];
+    const int p = tl.x * kGT + e / kGT, q = tl.y * kGT + e % kGT;
+    if (p < nv && q < nv) G[(size_t)p * nv + q] = s;
+}
+
+// Full Hermitian Gram matrix (host, nv x nv complex) of the nv vectors X.
+int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<double>>& G, cudaStream_t st) {
+    const int nt = (nv + kGT - 1) / kGT;
+    std::vector<int2> tiles;
+    for (int a = 0; a < nt; ++a)
+        for (int b = a; b < nt; ++b) tiles.push_back(make_int2(a, b));
+    const int ntile = (int)tiles.size();
+    int nz = std::max(1, std::min((nsm * 2 + ntile - 1) / ntile, (d + 4095) / 4096));
+    int2* dt = nullptr;
+    double2 *part = nullptr, *dG = nullptr;
+    int rc = KG_OK;
+    if (cudaMalloc(&dt, sizeof(int2) * ntile) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(double2) * (size_t)nz * ntile * kGT * kGT) != cudaSuccess ||
+        cudaMalloc(&dG, sizeof(double2) * (size_t)nv * nv) != cudaSuccess)
+        rc = KG_ENOMEM;
+    if (rc == KG_OK) {
+        cudaMemcpyAsync(dt, tiles.data(), sizeof(int2) * ntile, cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(dG, 0, sizeof(double2) * (size_t)nv * nv, st);
+        ProfScope ps("gram", st);
+        k_gram<<<dim3(ntile, nz), 256, 0, st>>>(X, nv, d, ntile, dt, part);
+        count_launch();
+        k_gram_reduce<<<dim3(ntile, (kGT * kGT + 255) / 256), 256, 0, st>>>(part, nz, ntile, dt, nv, dG);
+        count_launch();
+        std::vector<double2> h((size_t)nv * nv);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h.data(), dG, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "gram", __FILE__, __LINE__);
+        G.assign((size_t)nv * nv, 0.0);
+        for (int p = 0; p < nv; ++p)
+            for (int q = p; q < nv; ++q) {
+                const double2 v = h[(size_t)p * nv + q];
+                G[(size_t)p * nv + q] = std::complex<double>(v.x, v.y);
+                G[(size_t)q * nv + p] = std::complex<double>(v.x, -v.y);
+            }
+    }
+    cudaFree(dt);
+    cudaFree(part);
+    cudaFree(dG);
+    return rc;
+}
+
+}  // namespace kg
+
+// ------------------------------------------------------------- Keldysh
+struct KBlock {
+    int spin = 0, dagger = 0;
+    std::vector<int> idx;
+    kg_sector* nb = nullptr;
+    double2* store = nullptr;  // [n_t][na][d_nb]
+    double2* ovbuf = nullptr;  // [na][na]
+    kg::Krylov K;
+    kg::StepRunner R;
+    bool ready = false;
+};
+
+struct kg_keldysh {
+    kg_sector* ini = nullptr;
+    kg_sector* fin = nullptr;
+    std::vector<int> orb;
+    int n_orb = 0, n_t = 0, n_sub = 1;
+    double dt = 0.0;
+    kg_opts o;
+    double2* phi = nullptr;  // [n_t][d]
+    std::vector<KBlock> blocks;
+    std::vector<char> row_done;
+};
+
+namespace kg {
+
+static void block_release(KBlock& B) {
+    B.R.release();
+    krylov_free(B.K);
+    cudaFree(B.store);
+    cudaFree(B.ovbuf);
+    B.store = nullptr;
+    B.ovbuf = nullptr;
+    B.ready = false;
+}
+
+static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
+    if (B.ready) return KG_OK;
+    const int na = (int)B.idx.size(), dn = (int)B.nb->d;
+    KG_TRY(krylov_alloc(B.K, na, std::min(X->o.M, dn), dn, X->fin->nsm));
+    KG_CUDA(cudaMalloc(&B.store, sizeof(double2) * (size_t)X->n_t * na * dn));
+    KG_CUDA(cudaMalloc(&B.ovbuf, sizeof(double2) * (size_t)na * na));
+    StepPlan P;
+    P.sec = B.nb;
+    P.K = &B.K;
+    P.reorth = X->o.reorth;
+    P.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
+    KG_TRY(B.R.init(P, st, X->o.use_graphs != 0));
+    B.ready = true;
+    return KG_OK;
+}
+
+static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
+    const int na = (int)B.idx.size(), dn = (int)B.nb->d;
+    const double2* phik = X->phi + (size_t)k * X->fin->d;
+    for (int a = 0; a < na; ++a)
+        KG_TRY(launch_cop(X->fin, B.nb, X->orb[2 * B.idx[a]], B.spin, B.dagger, phik, B.K.vec(a, 0), st));
+    for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));
+    KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)k * na * dn, (size_t)dn * sizeof(double2), B.K.V,
+                              B.K.colV() * sizeof(double2), (size_t)dn * sizeof(double2), na,
+                              cudaMemcpyDeviceToDevice, st));
+    return KG_OK;
+}
+
+static int block_status(KBlock& B) {
+    std::vector<ColScalars> h(B.K.B);
+    KG_CUDA(cudaMemcpy(h.data(), B.K.cs, sizeof(ColScalars) * B.K.B, cudaMemcpyDeviceToHost));
+    for (auto& c : h)
+        if (c.status == KG_ENUMERIC) {
+            set_error("non-finite value during step (iii)");
+            return KG_ENUMERIC;
+        }
+    return KG_OK;
+}
+
+// Writes this block's part of G(t_k, t_l) for every stored k, l.
+static void block_assemble(kg_keldysh* X, KBlock& B, const std::vector<std::complex<double>>& Gm, double* G) {
+    const int na = (int)B.idx.size(), n = X->n_orb, nt = X->n_t, nv = nt * na;
+    for (int k = 0; k < nt; ++k)
+        for (int l = 0; l < nt; ++l)
+            for (int a = 0; a < na; ++a)
+                for (int ap = 0; ap < na; ++ap) {
+                    std::complex<double> g;
+                    if (!B.dagger)  // G^<_{a a'}(t_k,t_l) = i <Psi_a'(t_l) | Psi_a(t_k)>
+                        g = std::complex<double>(0.0, 1.0) * Gm[(size_t)(l * na + ap) * nv + (k * na + a)];
+                    else  // G^>_{a a'}(t_k,t_l) = -i <chi_a(t_k) | chi_a'(t_l)>
+                        g = std::complex<double>(0.0, -1.0) * Gm[(size_t)(k * na + a) * nv + (l * na + ap)];
+                    const size_t o = (((size_t)k * nt + l) * n + B.idx[a]) * n + B.idx[ap];
+                    G[2 * o] = g.real();
+                    G[2 * o + 1] = g.imag();
+                }
+}
+
+int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
+                   const kg_opts* o, kg_keldysh** out) {
+    *out = nullptr;
+    if (ini->L != fin->L || ini->nu != fin->nu || ini->nd != fin->nd) {
+        set_error("H_ini and H_fin must share (L, N_up, N_dn)");
+        return KG_EINVAL;
+    }
+    KG_TRY(check_orbitals(fin, orb, n_orb));
+    KG_TRY(check_opts(o));
+    if (n_t < 1 || !(dt >= 0.0)) {
+        set_error("bad time grid");
+        return KG_EINVAL;
+    }
+    KG_TRY(ensure_gs(ini, o));
+    cudaStream_t st = pick_stream(fin, o);
+    kg_keldysh* X = new kg_keldysh();
+    X->ini = ini;
+    X->fin = fin;
+    X->orb.assign(orb, orb + 2 * n_orb);
+    X->n_orb = n_orb;
+    X->dt = dt;
+    X->n_t = n_t;
+    X->o = *o;
+    X->n_sub = (o->dt_internal > 0.0) ? std::max(1, (int)std::lround(dt / o->dt_internal)) : 1;
+    X->row_done.assign(n_t, 0);
+    auto fail = [&](int r) {
+        keldysh_free(X);
+        return r;
+    };
+    const size_t d = (size_t)fin->d;
+    if (cudaMalloc(&X->phi, sizeof(double2) * n_t * d) != cudaSuccess) {
+        set_error("cannot hold Phi(t_k) for %d times", n_t);
+        return fail(KG_ENOMEM);
+    }
+    // step (ii): Phi(t_k) = e^{-iH t_k} |0>, stored on the grid
+    KG_CUDA(cudaMemcpyAsync(X->phi, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
+    if (n_t > 1) {
+        Krylov K;
+        StepRunner R;
+        int rc = krylov_alloc(K, 1, std::min(o->M, (int)d), (int)d, fin->nsm);
+        StepPlan P;
+        P.sec = fin;
+        P.K = &K;
+        P.reorth = o->reorth;
+        P.tau = dt / X->n_sub;
+        if (rc == KG_OK)
+            rc = cudaMemcpyAsync(K.V, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        if (rc == KG_OK) rc = R.init(P, st, o->use_graphs != 0);
+        for (int k = 1; rc == KG_OK && k < n_t; ++k) {
+            for (int n = 0; rc == KG_OK && n < X->n_sub; ++n) rc = R.run(st);
+            if (rc == KG_OK)
+                rc = cudaMemcpyAsync(X->phi + k * d, K.V, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                         ? KG_OK
+                         : KG_ECUDA;
+        }
+        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        R.release();
+        krylov_free(K);
+        if (rc != KG_OK) return fail(rc);
+    }
+    std::vector<int> idx[2];
+    groups(orb, n_orb, idx);
+    for (int spin = 0; spin < 2; ++spin) {
+        if (idx[spin].empty()) continue;
+        for (int dagger = 0; dagger < 2; ++dagger) {
+            kg_sector* nb = nullptr;
+            if (neighbour(fin, spin, dagger, &nb) != KG_OK) continue;  // that G part is zero
+            KBlock B;
+            B.spin = spin;
+            B.dagger = dagger;
+            B.idx = idx[spin];
+            B.nb = nb;
+            X->blocks.push_back(std::move(B));
+        }
+    }
+    *out = X;
+    return KG_OK;
+}
+
+void keldysh_free(kg_keldysh* X) {
+    if (!X) return;
+    for (auto& B : X->blocks) block_release(B);
+    cudaFree(X->phi);
+    delete X;
+}
+
+int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk) {
+    if (k < 0 || k >= X->n_t) {
+        set_error("row %d outside [0, %d)", k, X->n_t);
+        return KG_EINVAL;
+    }
+    cudaStream_t st = pick_stream(X->fin, &X->o);
+    const int n = X->n_orb;
+    if (G_les_kk) std::memset(G_les_kk, 0, sizeof(double) * 2 * n * n);
+    if (G_gtr_kk) std::memset(G_gtr_kk, 0, sizeof(double) * 2 * n * n);
+    for (auto& B : X->blocks) {
+        KG_TRY(block_prepare(X, B, st));
+        KG_TRY(block_row(X, B, k, st));
+        const int na = (int)B.idx.size(), dn = (int)B.nb->d;
+        KG_TRY(reset_slots(B.K, st));
+        const double2* xs = B.store + (size_t)k * na * dn;
+        KG_TRY(launch_overlaps_cs(B.K, xs, dn, xs, na, dn, B.ovbuf, 1, st));
+        std::vector<double2> h((size_t)na * na);
+        KG_CUDA(cudaMemcpyAsync(h.data(), B.ovbuf, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+        KG_CUDA(cudaStreamSynchronize(st));
+        KG_TRY(block_status(B));
+        double* G = B.dagger ? G_gtr_kk : G_les_kk;
+        if (!G) continue;
+        for (int bb = 0; bb < na; ++bb)
+            for (int a = 0; a < na; ++a) {
+                // h[bb][a] = <X_a | X_bb>
+                const double2 v = h[(size_t)bb * na + a];
+                const std::complex<double> ov(v.x, v.y);
+                int r, c;
+                std::complex<double> g;
+                if (!B.dagger) {  // G^<_{bb a} = i <Psi_a | Psi_bb>
+                    r = B.idx[bb];
+                    c = B.idx[a];
+                    g = std::complex<double>(0.0, 1.0) * ov;
+                } else {  // G^>_{a bb} = -i <chi_a | chi_bb>
+                    r = B.idx[a];
+                    c = B.idx[bb];
+                    g = std::complex<double>(0.0, -1.0) * ov;
+                }
+                G[2 * ((size_t)r * n + c)] = g.real();
+                G[2 * ((size_t)r * n + c) + 1] = g.imag();
+            }
+    }
+    X->row_done[k] = 1;
+    return KG_OK;
+}
+
+int keldysh_gram(kg_keldysh* X, double* G_les, double* G_gtr) {
+    for (int k = 0; k < X->n_t; ++k)
+        if (!X->row_done[k]) {
+            set_error("row %d of step (iii) not computed", k);
+            return KG_EINVAL;
+        }
+    cudaStream_t st = pick_stream(X->fin, &X->o);
+    const size_t tot = (size_t)X->n_t * X->n_t * X->n_orb * X->n_orb * 2;
+    if (G_les) std::memset(G_les, 0, sizeof(double) * tot);
+    if (G_gtr) std::memset(G_gtr, 0, sizeof(double) * tot);
+    for (auto& B : X->blocks) {
+        double* G = B.dagger ? G_gtr : G_les;
+        if (!G) continue;
+        const int na = (int)B.idx.size();
+        std::vector<std::complex<double>> Gm;
+        KG_TRY(gram(B.store, X->n_t * na, (int)B.nb->d, X->fin->nsm, Gm, st));
+        block_assemble(X, B, Gm, G);
+    }
+    return KG_OK;
+}
+
+int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in) {
+    if (k < 0 || k >= X->n_t) {
+        set_error("row %d outside [0, %d)", k, X->n_t);
+        return KG_EINVAL;
+    }
+    cudaStream_t st = pick_stream(X->fin, &X->o);
+    const size_t d = (size_t)X->fin->d;
+    if (phi_host) KG_CUDA(cudaMemcpyAsync(phi_host, X->phi + k * d, sizeof(double2) * d, cudaMemcpyDeviceToHost, st));
+    if (phi_in) KG_CUDA(cudaMemcpyAsync(X->phi + k * d, phi_in, sizeof(double2) * d, cudaMemcpyHostToDevice, st));
+    KG_CUDA(cudaStreamSynchronize(st));
+    return KG_OK;
+}
+
+// Whole Keldysh calculation, one (spin, kind) block at a time so that only
+// one block's stored columns are resident.
+int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
+                  const kg_opts* o, double* G_les, double* G_gtr) {
+    if (!G_les || !G_gtr) {
+        set_error("NULL output");
+        return KG_EINVAL;
+    }
+    kg_keldysh* X = nullptr;
+    KG_TRY(keldysh_create(ini, fin, orb, n_orb, dt, n_t, o, &X));
+    cudaStream_t st = pick_stream(fin, o);
+    const size_t tot = (size_t)n_t * n_t * n_orb * n_orb * 2;
+    std::memset(G_les, 0, sizeof(double) * tot);
+    std::memset(G_gtr, 0, sizeof(double) * tot);
+    int rc = KG_OK;
+    for (auto& B : X->blocks) {
+        rc = block_prepare(X, B, st);
+        for (int k = 0; rc == KG_OK && k < n_t; ++k) rc = block_row(X, B, k, st);
+        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        if (rc == KG_OK) rc = block_status(B);
+        std::vector<std::complex<double>> Gm;
+        if (rc == KG_OK) rc = gram(B.store, n_t * (int)B.idx.size(), (int)B.nb->d, fin->nsm, Gm, st);
+        if (rc == KG_OK) block_assemble(X, B, Gm, B.dagger ? G_gtr : G_les);
+        block_release(B);
+        if (rc != KG_OK) break;
+    }
+    keldysh_free(X);
+    return rc;
+}
+
+}  // namespace kg

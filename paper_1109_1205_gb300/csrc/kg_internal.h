@@ -1,0 +1,319 @@
+// kg_internal.h -- shared declarations of the CUDA implementation of
+// libkrylovgf (not part of the public ABI; see include/krylovgf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "krylovgf.h"
+
+namespace kg {
+
+constexpr int kMaxL = 32;      // spin strings are 32-bit words
+constexpr int kMaxM = 64;      // Krylov dimension of one propagation step
+constexpr int kMaxMgs = 256;   // Krylov dimension of one ground-state restart
+constexpr int kChunk = 32;     // complex dot products accumulated per pass
+constexpr int kMaxOv = 32;     // overlap vectors fused into the combination pass
+constexpr int kPart = 72;      // doubles per block in a partial-sum row
+constexpr int kThreads = 256;  // threads per block of the streaming kernels
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+void count_launch(unsigned long long n = 1);
+
+#define KG_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return kg::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define KG_LAUNCHED()                                                   \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return kg::cuda_fail(e_, "kernel launch", __FILE__, __LINE__); \
+        kg::count_launch();                                             \
+    } while (0)
+
+#define KG_TRY(call)                        \
+    do {                                    \
+        int r_ = (call);                    \
+        if (r_ != KG_OK) return r_;         \
+    } while (0)
+
+// ------------------------------------------------------- sector (device)
+// One spin species: the D strings with N of L bits set, in rank order, and
+// the CSR list of allowed hops.  For string s, entry e = (j, code) says that
+// h_ab c^dag_a c_b maps string j onto s, a = (code & 1023) / L, b = code % L
+// (within the low 10 bits), with fermion sign (-1)^(code >> 31).
+struct SpinTables {
+    int D = 0, N = 0;
+    long long nnz = 0;
+    int max_row = 0;
+    uint32_t* bits = nullptr;  // [D]
+    int* off = nullptr;        // [D + 1]
+    uint2* ent = nullptr;      // [nnz]
+    double* e = nullptr;       // [D]  sum over occupied i of (eps_i + h_ii)
+};
+
+// Read-only view of a sector, passed by value to kernels.
+struct SecView {
+    int L, Du, Dd, d;
+    const uint32_t* up_bits;
+    const uint32_t* dn_bits;
+    const int* up_off;
+    const uint2* up_ent;
+    const double* up_e;
+    const int* dn_off;
+    const uint2* dn_ent;
+    const double* dn_e;
+    const double2* hamp;  // [L*L] hopping amplitudes h_ab
+    const double* Utab;   // [nchunk * 256] U summed over the set bits of a byte
+    int nchunk;
+    int hopmode;          // 0: all hops share the real amplitude h0; 1: real; 2: complex
+    double h0;
+    uint32_t du_m;        // s / D_up = (umulhi(s, du_m) + s) >> du_l   (s < 2^31)
+    int du_l;
+};
+
+}  // namespace kg
+
+struct kg_sector {
+    int L = 0, nu = 0, nd = 0;
+    int Du = 0, Dd = 0;
+    long long d = 0;
+    std::vector<double> h_re, h_im, eps, U;
+    int hopmode = 1;
+    double h0 = 0.0;
+    kg::SpinTables up, dn;
+    double2* hamp = nullptr;
+    double* Utab = nullptr;
+    int nchunk = 1;
+    kg_sector* nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][dagger]
+    bool is_child = false;
+    cudaStream_t stream = nullptr;   // the library's own stream (graph capture)
+    cudaEvent_t fence = nullptr;     // orders it after the legacy default stream
+    int device = 0;
+    int nsm = 148;
+    bool has_gs = false;
+    double E0 = 0.0, resid = 0.0, gap = 0.0;
+    double2* gs = nullptr;  // [d] cached ground state (unit norm)
+    kg::SecView view() const;
+};
+
+namespace kg {
+
+// --------------------------------------------------- Krylov workspace
+// Per-column scalars of the Lanczos recursion, Eq. (recursion), kept on the
+// device so that a whole propagation step runs without a host round trip.
+struct ColScalars {
+    double alpha[kMaxMgs];      // a_k (diagonal of T)
+    double beta[kMaxMgs + 1];   // b_k (beta[k] couples vectors k-1 and k)
+    double scale[kMaxMgs + 1];  // 1/||V_k||: stored Lanczos vectors are unnormalised
+    double2 h[kMaxMgs + 1];     // Gram-Schmidt coefficients of the current pass
+    double2 c[kMaxMgs];         // combination coefficients (already times scale)
+    double beta0;               // norm of the start vector
+    double lam0, lam1, resest;  // ground-state Ritz value, next one, residual estimate
+    double rq, rnorm;           // Rayleigh quotient and residual of a Ritz vector
+    double ovnorm;              // norm of the last combined vector
+    int m_eff;                  // Krylov dimension reached (smaller after a breakdown)
+    int status;                 // KG_OK, KG_ENUMERIC or KG_ENOCONV
+    int ov_slot;                // overlap rows written so far
+    int pad;
+};
+
+// B independent columns (vectors) of one sector, each with its own Lanczos
+// basis V[b][0..M] of dimension d.
+struct Krylov {
+    int B = 0, M = 0, d = 0;
+    int nblk = 1;               // blocks per column of the streaming kernels
+    double2* V = nullptr;       // [B][M+1][d]
+    double2* W = nullptr;       // [B][d]
+    ColScalars* cs = nullptr;   // [B]
+    double* part = nullptr;     // [B][nblk][kPart]
+    unsigned* cnt = nullptr;    // [B]
+    double* Q = nullptr;        // [B][M*M] eigenvectors of T
+    size_t colV() const { return (size_t)(M + 1) * (size_t)d; }
+    double2* vec(int b, int k) const { return V + (size_t)b * colV() + (size_t)k * d; }
+};
+
+int krylov_alloc(Krylov& K, int B, int M, int d, int nsm);
+void krylov_free(Krylov& K);
+
+// ----------------------------------------------------------- launchers
+// a2: y = H x (plain).
+int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st);
+// a2+a3: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
+// partial sums of a_j = <v_j, w> reduced on the device.
+int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, cudaStream_t st);
+// start of a step: beta0 = ||V_0||, scale[0], m_eff = M, status reset.
+int launch_colnorm(Krylov& K, cudaStream_t st);
+// a3 reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or
+// h_k = <v_k, V_{j+1}> (second pass) for k in [k0, k0 + nk).
+int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st);
+// a3 update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
+// second pass), then b_{j+1} = ||V_{j+1}||, scale, breakdown test.
+int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st);
+// a4: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1;
+// mode 1: ground-state Ritz pair (lam0, c = q_0).
+int launch_tridiag(Krylov& K, int mode, double tau, cudaStream_t st);
+// a5 + a7: out_b = sum_k c_k V_k; ||out_b||; overlaps <ov_a, out_b>.
+int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov, int n_ov,
+                   size_t ov_stride, double2* ov_out, int ov_rows, bool renorm_v0,
+                   cudaStream_t st);
+// overlaps of arbitrary vectors: out[b][a] = <ov_a, x_b> (a7), one slot.
+int launch_overlaps(int B, int d, const double2* x, size_t x_stride, const double2* ov, int n_ov,
+                    size_t ov_stride, double2* out, double* part, unsigned* cnt, int nblk,
+                    cudaStream_t st);
+// a6: y = c / c^dag x between neighbouring sectors.
+int launch_cop(const kg_sector* src, const kg_sector* dst, int site, int spin, int dagger,
+               const double2* x, double2* y, cudaStream_t st);
+// utilities
+int launch_random_start(double2* v, int d, unsigned long long seed, cudaStream_t st);
+int launch_scale_copy(double2* dst, const double2* src, int d, double s, cudaStream_t st);
+
+// ------------------------------------------------------------ drivers
+int sector_build(int L, int nu, int nd, const double* h_re, const double* h_im, const double* eps,
+                 const double* U, kg_sector** out);
+void sector_free(kg_sector* s);
+int neighbour(kg_sector* s, int spin, int dagger, kg_sector** out);
+cudaStream_t pick_stream(const kg_sector* s, const kg_opts* o);
+
+// One propagation step exp(-i H tau) of every column of K, starting from
+// V[b][0] and leaving the result in V[b][0] (a2-a5).  Optional fused
+// overlaps of the result with n_ov vectors.
+struct StepPlan {
+    const kg_sector* sec = nullptr;
+    Krylov* K = nullptr;
+    int reorth = 1;
+    double tau = 0.0;
+    const double2* ov = nullptr;
+    int n_ov = 0;
+    size_t ov_stride = 0;
+    double2* ov_out = nullptr;
+    int ov_rows = 0;
+};
+int enqueue_step(const StepPlan& P, cudaStream_t st);
+
+int ground_state(kg_sector* s, const kg_opts* o);
+int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
+                      double* G_gtr, double* G_les);
+int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
+                   const kg_opts* o, kg_keldysh** out);
+void keldysh_free(kg_keldysh* X);
+int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk);
+int keldysh_gram(kg_keldysh* X, double* G_les, double* G_gtr);
+int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in);
+int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
+                  const kg_opts* o, double* G_les, double* G_gtr);
+int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o);
+void set_capturing(bool on);
+bool profiling();
+
+// Opt-in per-kernel timing: while the profiler is on, every launcher brackets
+// its launch with CUDA events on the launch stream (graphs are not used).
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t st = nullptr;
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+};
+int profile_start();
+int profile_stop();
+int profile_count();
+int profile_get(int i, char* name, int len, long long* launches, double* ms);
+int probe_fp64(double* tflops, cudaStream_t st);
+unsigned long long launch_count();
+const char* last_error();
+
+}  // namespace kg
+
+// ----------------------------------------------------- device helpers
+#ifdef __CUDACC__
+namespace kg {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cdotmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+// s / D_up and s % D_up without a hardware divide (multiply-high method).
+__device__ __forceinline__ void split_index(const SecView& S, int s, int& i_dn, int& i_up) {
+    i_dn = (int)((__umulhi((unsigned)s, S.du_m) + (unsigned)s) >> S.du_l);
+    i_up = s - i_dn * S.Du;
+}
+
+// FP64 -> FP32 by truncation on the integer pipe (no FP64 instruction):
+// exponent rebias and the top 23 mantissa bits; |x| < 2^-126 gives 0.  Used
+// only for correction terms whose size makes the truncation negligible.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned bits = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return e > 0 ? __uint_as_float(bits) : 0.0f;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums nv doubles over the block.  v: this thread's values; sm: shared
+// scratch of (blockDim/32)*nv doubles; on return out[0..nv) (shared) holds
+// the block totals (valid for all threads).
+template <int NV>
+__device__ __forceinline__ void block_sum(const double (&v)[NV], int nv, double* sm, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+            double s = warp_sum(v[k]);
+            if (lane == 0) sm[warp * nv + k] = s;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sm[w * nv + k];
+        out[k] = s;
+    }
+    __syncthreads();
+}
+
+// Deterministic grid reduction.  Each block stores its nv totals (bsum, in
+// shared memory) into its row of part; the last block to arrive (atomic
+// ticket) sums the rows in a fixed order into red (shared, nv doubles),
+// resets the ticket and returns true.  Other blocks return false.
+__device__ __forceinline__ bool grid_finish(const double* bsum, int nv, double* part, unsigned* cnt,
+                                            int nblk, double* red) {
+    __shared__ unsigned ticket;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) part[(size_t)blockIdx.x * kPart + k] = bsum[k];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
+    __syncthreads();
+    if (ticket != (unsigned)(nblk - 1)) return false;
+    __threadfence();
+    // value k is summed by one warp: lanes take blocks lane, lane+32, ...
+    // then a fixed shuffle tree -- the order does not depend on timing.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nv; k += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)b * kPart + k);
+        s = warp_sum(s);
+        if (lane == 0) red[k] = s;
+    }
+    if (threadIdx.x == 0) *cnt = 0u;
+    __syncthreads();
+    return true;
+}
+
+}  // namespace kg
+#endif

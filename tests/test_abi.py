@@ -1,0 +1,81 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function
+that include/krylovgf.h declares, and rejects bad arguments before touching
+the GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "krylovgf.h")
+
+
+@pytest.fixture(scope="module")
+def kg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1109_1205_gb300 as kg
+    return kg
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["kg_build_sector", "kg_ground_state", "kg_green_equilibrium", "kg_green_keldysh",
+                     "kg_hpsi", "kg_apply_cop", "kg_propagate"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(kg):
+    lib = ctypes.CDLL(kg.library_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", kg.library_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (kg_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_options_and_status_strings(kg):
+    o = kg.kg_opts_default()
+    assert (o.M, o.M_gs, o.reorth, o.use_graphs, o.seed) == (20, 100, 1, 1, 1234)
+    assert o.tol_resid == 1e-12 and o.stream is None
+    for code in range(0, -9, -1):
+        assert kg.kg_strerror(code) != "unknown status"
+    assert kg.kg_strerror(-42) == "unknown status"
+
+
+def test_argument_validation_before_device_use(kg):
+    lib = kg.lib
+    out = ctypes.c_void_p()
+    z = np.zeros(64)
+    # bad sizes
+    for L, nu, nd in [(0, 0, 0), (33, 1, 1), (4, 5, 1), (4, 1, -1)]:
+        rc = lib.kg_build_sector(L, nu, nd, z.ctypes.data, None, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
+        assert rc == kg.KG_EINVAL
+    # non-Hermitian hopping
+    h = np.array([[0.0, 1.0], [2.0, 0.0]])
+    rc = lib.kg_build_sector(2, 1, 1, h.ctypes.data, None, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
+    assert rc == kg.KG_EINVAL and "Hermitian" in kg.kg_last_error()
+    # complex hopping must be anti-symmetric in its imaginary part
+    hi = np.array([[0.0, 0.5], [0.5, 0.0]])
+    hr = np.array([[0.0, 1.0], [1.0, 0.0]])
+    rc = lib.kg_build_sector(2, 1, 1, hr.ctypes.data, hi.ctypes.data, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
+    assert rc == kg.KG_EINVAL
+    # dimension beyond 2^31
+    big = np.zeros(32 * 32)
+    rc = lib.kg_build_sector(32, 16, 16, big.ctypes.data, None, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
+    assert rc == kg.KG_ENOMEM
+    # NULL handles are rejected, never dereferenced
+    assert lib.kg_hpsi(None, None, None, None) == kg.KG_EINVAL
+    assert lib.kg_ground_state(None, None, None, None, None) == kg.KG_EINVAL
+    assert lib.kg_keldysh_row(None, 0, None, None) == kg.KG_EINVAL
+    lib.kg_free_sector(None)
+    lib.kg_keldysh_free(None)

@@ -1,0 +1,301 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: integer/index work (strings, c/c^dag maps) bit-exact; H*psi to
+1e-12 relative (one FP64 summation order against another); propagated
+vectors 1e-11 absolute (unit vectors, tens of Krylov steps); ground-state
+energy 1e-12 relative and Green's functions 1e-10 absolute (the stated
+parity bar of this path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1109_1205_gb300 as kg  # noqa: E402
+
+G_TOL = 1e-10
+E_TOL = 1e-12
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def stream():
+    return torch.cuda.current_stream()
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
+
+
+# --------------------------------------------------------------- a1 ranking
+@pytest.mark.parametrize("L,nu,nd", [(1, 0, 1), (6, 3, 2), (12, 6, 6), (16, 7, 8), (20, 3, 17)])
+def test_strings_are_rank_ordered(L, nu, nd):
+    s = kg.Sector(W.hubbard_ring(L, 1.0, nu, nd))
+    up, dn = s.strings()
+    for arr, n in ((up, nu), (dn, nd)):
+        assert len(arr) == math.comb(L, n)
+        if L <= 16:
+            ref = np.array(sorted(x for x in range(1 << L) if bin(x).count("1") == n), dtype=np.uint32)
+            assert np.array_equal(arr, ref)
+        else:
+            assert np.all(np.diff(arr.astype(np.int64)) > 0)
+            assert all(bin(int(x)).count("1") == n for x in arr[:: max(1, len(arr) // 997)])
+    assert s.dim == math.comb(L, nu) * math.comb(L, nd)
+
+
+# ------------------------------------------------------------------ a2 H*psi
+HPSI_MODELS = [
+    ("complex", W.random_model(6, 3, 2, seed=1, complex_hopping=True)),
+    ("real-nonuniform", W.random_model(8, 4, 3, seed=2, complex_hopping=False, density=0.6)),
+    ("ring-uniform", W.hubbard_ring(10, 4.0, 5, 4)),
+    ("c1-star", W.config_c1()["model"]),
+    ("chain-field", W.siam_chain(9, 3.0, 4, 5, field=0.7)),
+    ("c2-ring-full", W.config_c2()["fin"]),
+]
+
+
+@pytest.mark.parametrize("name,model", HPSI_MODELS, ids=[m[0] for m in HPSI_MODELS])
+def test_hpsi_parity(name, model):
+    s = kg.Sector(model)
+    o = oracle.Sector(model)
+    assert s.dim == o.dim
+    x = W.random_state(s.dim, 7)
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    s.hpsi(xd, yd, stream())
+    y = host(yd)
+    ref = o.hpsi(x)
+    assert relerr(y, ref) < 1e-12, name
+
+
+def test_hpsi_linearity_and_hermiticity():
+    m = W.random_model(7, 3, 3, seed=4, complex_hopping=True)
+    s = kg.Sector(m)
+    x, z = W.random_state(s.dim, 1), W.random_state(s.dim, 2)
+    yx, yz = torch.empty(s.dim, dtype=torch.complex128, device="cuda"), torch.empty(s.dim, dtype=torch.complex128,
+                                                                                 device="cuda")
+    s.hpsi(dev(x), yx, stream())
+    s.hpsi(dev(z), yz, stream())
+    hx, hz = host(yx), host(yz)
+    assert abs(np.vdot(z, hx) - np.vdot(hz, x)) < 1e-12
+
+
+# ------------------------------------------------------------ a6 c / c^dag
+def test_cop_bit_exact():
+    m = W.random_model(6, 3, 2, seed=9, complex_hopping=True)
+    s = kg.Sector(m)
+    o = oracle.Sector(m)
+    x = W.random_state(s.dim, 3)
+    xd = dev(x)
+    for spin in (0, 1):
+        for dagger in (False, True):
+            on = o.neighbour(spin, dagger)
+            dn = s.neighbour_dim(spin, dagger)
+            assert dn == on.dim
+            for site in range(6):
+                yd = torch.empty(dn, dtype=torch.complex128, device="cuda")
+                s.apply_cop(site, spin, dagger, xd, yd, stream())
+                assert np.array_equal(host(yd), o.apply_cop(on, site, spin, dagger, x)), (site, spin, dagger)
+
+
+def test_cop_missing_neighbour_is_einval():
+    s = kg.Sector(W.hubbard_ring(4, 1.0, 4, 0))
+    with pytest.raises(kg.KGError) as e:
+        s.neighbour_dim(0, True)  # N_up = L: no room for c^dag_up
+    assert e.value.code == kg.KG_EINVAL
+    with pytest.raises(kg.KGError):
+        s.neighbour_dim(1, False)  # N_dn = 0: nothing to annihilate
+
+
+# ---------------------------------------------------------- a3-a5 ground state
+GS_MODELS = [
+    ("c1", W.config_c1()["model"]),
+    ("complex-L7", W.random_model(7, 3, 4, seed=5, complex_hopping=True)),
+    ("ring-L10", W.hubbard_ring(10, 4.0, 5, 5)),
+    ("chain-field", W.siam_chain(8, 1.0, 4, 4, field=0.2)),
+    ("tiny-d1", W.make_model(2, 2, 0, W.chain_hopping(2), None, [1.0, 2.0])),
+    ("d-below-M", W.random_model(4, 1, 2, seed=3)),
+]
+
+
+@pytest.mark.parametrize("name,model", GS_MODELS, ids=[m[0] for m in GS_MODELS])
+def test_ground_state_parity(name, model):
+    s = kg.Sector(model)
+    E0, res, _ = s.ground_state()
+    e_or, psi_or, _ = oracle.Sector(model).ground_state()
+    assert abs(E0 - e_or) <= E_TOL * max(1.0, abs(e_or)), (E0, e_or)
+    assert res <= 1e-12 * max(1.0, abs(E0))
+    psi = s.ground_state_vector()
+    assert abs(np.linalg.norm(psi) - 1) < 1e-13
+    assert abs(abs(np.vdot(psi_or, psi)) - 1) < 1e-10
+
+
+# ------------------------------------------------------------ propagation
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+@pytest.mark.parametrize("dt,n", [(0.05, 20), (-0.05, 12), (0.1, 5)])
+def test_propagate_parity(reorth, dt, n):
+    m = W.random_model(7, 3, 3, seed=11, complex_hopping=True)
+    s = kg.Sector(m)
+    o = oracle.Sector(m)
+    x = W.random_state(s.dim, 5)
+    xd = dev(x)
+    s.propagate(xd, dt, n, kg.kg_opts_default(reorth=reorth))
+    y = host(xd)
+    ref = o.propagate(x, dt * n)
+    assert np.max(np.abs(y - ref)) < 1e-11
+    assert abs(np.linalg.norm(y) - 1) < 1e-12
+
+
+def test_propagate_large_sector_and_graphs():
+    m = W.hubbard_ring(10, 4.0, 5, 4)
+    s = kg.Sector(m)
+    o = oracle.Sector(m)
+    x = W.random_state(s.dim, 6)
+    for graphs in (0, 1):
+        xd = dev(x)
+        s.propagate(xd, 0.05, 8, kg.kg_opts_default(use_graphs=graphs))
+        assert np.max(np.abs(host(xd) - o.propagate(x, 0.4))) < 1e-11
+
+
+# ------------------------------------------------------- equilibrium G
+def test_green_equilibrium_c1_full():
+    cfg = W.config_c1()
+    s = kg.Sector(cfg["model"])
+    opts = kg.kg_opts_default(M=cfg["M"], M_gs=cfg["M"])
+    Gg, Gl = s.green_equilibrium(cfg["orbitals"], cfg["dt"], cfg["n_steps"], opts)
+    rg, rl, _ = oracle.green_equilibrium(cfg["model"], cfg["orbitals"], cfg["dt"], cfg["n_steps"])
+    assert np.max(np.abs(Gg - rg)) < G_TOL
+    assert np.max(np.abs(Gl - rl)) < G_TOL
+    # sum rule at t = 0
+    assert abs(1j * (Gg[0, 0, 0] - Gl[0, 0, 0]) - 1) < 1e-12
+
+
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+def test_green_equilibrium_both_spins(reorth):
+    m = W.random_model(6, 3, 2, seed=21, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (5, 0), (1, 1), (4, 1)]
+    s = kg.Sector(m)
+    Gg, Gl = s.green_equilibrium(orbs, 0.1, 30, kg.kg_opts_default(reorth=reorth))
+    rg, rl, _ = oracle.green_equilibrium(m, orbs, 0.1, 30)
+    assert np.max(np.abs(Gg - rg)) < G_TOL
+    assert np.max(np.abs(Gl - rl)) < G_TOL
+
+
+def test_green_equilibrium_edge_sectors():
+    # full up band: no particle part for spin up; empty down band: no hole part
+    m = W.make_model(3, 3, 0, W.chain_hopping(3), None, [2.0, 1.0, 0.5])
+    s = kg.Sector(m)
+    orbs = [(0, 0), (1, 1)]
+    Gg, Gl = s.green_equilibrium(orbs, 0.2, 6)
+    rg, rl, _ = oracle.green_equilibrium(m, orbs, 0.2, 6)
+    assert np.max(np.abs(Gg - rg)) < G_TOL and np.max(np.abs(Gl - rl)) < G_TOL
+    assert np.all(Gg[:, 0, 0] == 0) and np.all(Gl[:, 1, 1] == 0)
+
+
+def test_hubbard_atom_on_gpu():
+    U = 2.6
+    for nu, nd in ((1, 0), (0, 1), (1, 1)):
+        m = W.make_model(1, nu, nd, np.zeros((1, 1)), np.full((2, 1), -U / 2), np.array([U]))
+        Gg, Gl = kg.Sector(m).green_equilibrium([(0, 0), (0, 1)], 0.25, 8)
+        rg, rl, _ = oracle.green_equilibrium(m, [(0, 0), (0, 1)], 0.25, 8)
+        assert np.max(np.abs(Gg - rg)) < 1e-13 and np.max(np.abs(Gl - rl)) < 1e-13
+
+
+# ------------------------------------------------------------- Keldysh G
+def keldysh_case():
+    ini = W.siam_chain(6, 2.0, 3, 3, field=0.3)
+    fin = W.siam_chain(6, 2.0, 3, 3, field=0.0)
+    orbs = [(i, 0) for i in range(6)] + [(i, 1) for i in range(6)]
+    return ini, fin, orbs
+
+
+def test_keldysh_parity_and_staged_api():
+    ini, fin, orbs = keldysh_case()
+    dt, nt = 0.1, 10
+    si, sf = kg.Sector(ini), kg.Sector(fin)
+    Gl, Gg = kg.kg_green_keldysh(si.handle, sf.handle, orbs, dt, nt)
+    rl, rg, _ = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    assert np.max(np.abs(Gl - rl)) < G_TOL
+    assert np.max(np.abs(Gg - rg)) < G_TOL
+    # staged: rows (in any order), then the Gram, equal the one-shot call
+    K = kg.Keldysh(si, sf, orbs, dt, nt)
+    for k in reversed(range(nt)):
+        dl, dg = K.row(k)
+        assert np.max(np.abs(dl - rl[k, k])) < G_TOL and np.max(np.abs(dg - rg[k, k])) < G_TOL
+    Sl, Sg = K.gram()
+    assert np.max(np.abs(Sl - Gl)) < 1e-12 and np.max(np.abs(Sg - Gg)) < 1e-12
+    K.close()
+
+
+def test_keldysh_gram_needs_all_rows():
+    ini, fin, orbs = keldysh_case()
+    si, sf = kg.Sector(ini), kg.Sector(fin)
+    K = kg.Keldysh(si, sf, orbs[:2], 0.1, 4)
+    K.row(0)
+    with pytest.raises(kg.KGError) as e:
+        K.gram()
+    assert e.value.code == kg.KG_EINVAL
+    K.close()
+
+
+def test_keldysh_internal_substeps_and_phi_roundtrip():
+    ini, fin, orbs = keldysh_case()
+    orbs = [(0, 0), (3, 0), (0, 1)]
+    si, sf = kg.Sector(ini), kg.Sector(fin)
+    opts = kg.kg_opts_default(dt_internal=0.1)
+    Gl, Gg = kg.kg_green_keldysh(si.handle, sf.handle, orbs, 0.3, 5, opts)
+    rl, rg, _ = oracle.green_keldysh(ini, fin, orbs, 0.3, 5)
+    assert np.max(np.abs(Gl - rl)) < G_TOL and np.max(np.abs(Gg - rg)) < G_TOL
+    K = kg.Keldysh(si, sf, orbs, 0.3, 5, opts)
+    phi = K.get_phi(4)
+    K.set_phi(4, phi)
+    dl, dg = K.row(4)
+    assert np.max(np.abs(dl - rl[4, 4])) < G_TOL and np.max(np.abs(dg - rg[4, 4])) < G_TOL
+    K.close()
+
+
+def test_keldysh_mismatched_sectors():
+    a = kg.Sector(W.hubbard_ring(4, 1.0, 2, 2))
+    b = kg.Sector(W.hubbard_ring(4, 1.0, 2, 1))
+    with pytest.raises(kg.KGError) as e:
+        kg.kg_green_keldysh(a.handle, b.handle, [(0, 0)], 0.1, 3)
+    assert e.value.code == kg.KG_EINVAL
+
+
+# ------------------------------------------- full-size c2, sampled entries
+def test_c2_full_size_sampled():
+    """The Hubbard-ring quench at its full size (d = 853,776), in the launch
+    configuration of the benchmark: E0 of H_ini, and sampled entries of the
+    time-diagonal blocks G(t_k, t_k) against the oracle computed one by one."""
+    cfg = W.config_c2()
+    si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+    opts = kg.kg_opts_default(M=cfg["M"])
+    E0, res, _ = si.ground_state(opts)
+    osec = oracle.Sector(cfg["ini"])
+    e_or, psi_or, _ = osec.ground_state()
+    assert abs(E0 - e_or) <= E_TOL * abs(e_or)
+    K = kg.Keldysh(si, sf, cfg["orbitals"], cfg["dt"], cfg["n_t"], opts)
+    for k in (0, 3):
+        dl, dg = K.row(k)
+        for (a, b) in ((0, 0), (0, 5)):
+            les, gtr = oracle.keldysh_entry(cfg["ini"], cfg["fin"], cfg["orbitals"][a], cfg["orbitals"][b],
+                                            cfg["dt"], k, k, gs=(e_or, psi_or, 0.0))
+            assert abs(dl[a, b] - les) < G_TOL and abs(dg[a, b] - gtr) < G_TOL, (k, a, b)
+        # half filling + particle-hole symmetry of the ring: n_i(t) = 1/2
+        assert np.max(np.abs((-1j * np.diag(dl)).real - 0.5)) < 1e-10
+    K.close()
