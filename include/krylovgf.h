@@ -71,7 +71,9 @@ typedef struct kg_opts {
                            Gram-Schmidt pass against every stored Lanczos
                            vector; 2: plus two passes (1)                       */
     int batch;          /* columns per batched propagation launch, 0 = all (0) */
-    int schedule;       /* H*psi schedule; 0 = autotuned (0)                    */
+    int schedule;       /* H*psi hop sums: 0 = exact 64-bit integer sums when
+                           all hops share one amplitude (else FP64), 1 = FP64
+                           sums always (0)                                      */
     int use_graphs;     /* replay each propagation step as a CUDA graph (1)    */
     double dt_internal; /* Keldysh: Krylov step inside one grid step; 0 = dt   */
     unsigned long long seed; /* ground-state start vector seed (1234)         */

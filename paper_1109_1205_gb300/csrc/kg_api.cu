@@ -27,6 +27,7 @@ int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o
     P.sec = s;
     P.K = &K;
     P.reorth = o->reorth;
+    P.int_hops = o->schedule != 1;
     P.tau = dt;
     if (rc == KG_OK)
         rc = cudaMemcpyAsync(K.V, x, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;

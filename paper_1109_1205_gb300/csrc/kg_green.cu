@@ -158,6 +158,7 @@ int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_
             P.sec = nb;
             P.K = &K;
             P.reorth = o->reorth;
+            P.int_hops = o->schedule != 1;
             P.tau = dagger ? dt : -dt;  // particle: e^{-iHt}; hole: e^{+iHt}
             P.ov = chi;
             P.n_ov = na;
@@ -368,6 +369,7 @@ static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
     P.sec = B.nb;
     P.K = &B.K;
     P.reorth = X->o.reorth;
+    P.int_hops = X->o.schedule != 1;
     P.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
     KG_TRY(B.R.init(P, st, X->o.use_graphs != 0));
     B.ready = true;
@@ -459,6 +461,7 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
         P.sec = fin;
         P.K = &K;
         P.reorth = o->reorth;
+        P.int_hops = o->schedule != 1;
         P.tau = dt / X->n_sub;
         if (rc == KG_OK)
             rc = cudaMemcpyAsync(K.V, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;

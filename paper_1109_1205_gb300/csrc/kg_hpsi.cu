@@ -8,16 +8,39 @@
 //
 // Up hops gather inside one row (L1/L2 resident); down hops read whole rows
 // at a stride of D_up, so a warp (consecutive i_up, one i_dn) walks the same
-// down-hop list and its loads are coalesced.  Fermion signs are applied by
-// flipping the IEEE sign bit with integer XOR, and for uniform hopping the
-// amplitude multiplies the whole hop sum once, so the FP64 pipe sees one add
-// per hop and component.
+// down-hop list and its loads are coalesced.
+//
+// Hop sums.  The FP64 pipe of this GPU issues about two lanes per clock per
+// SM, 64 times fewer than the integer pipe.  When every hop has the same
+// amplitude h0 (the Hubbard ring and the SIAM chain), the hop part is h0 times
+// a signed sum of gathered components, which is computed exactly on the
+// integer pipe: each component becomes the 64-bit fixed-point number
+// round(x * 2^(1075 + P - E)), E the largest exponent field of the vector and
+// P = 9 - ceil(log2(hops + 1)) the head room, so no sum can overflow.  The
+// sum is exact; the only rounding is the conversion of each term, at most
+// 2^-57 of the vector's largest component, and one conversion back to FP64.
+// Other hoppings (site-dependent or complex amplitudes) use FP64 FMAs.
+#include <algorithm>
+
 #include "kg_internal.h"
 
 namespace kg {
 
 __device__ __forceinline__ double flip(double v, uint32_t code) {
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(code >> 31) << 63));
+}
+
+// Fixed-point image of x with the vector's largest exponent field E and
+// pre-shift P; the hop sign `neg` (0/1) is applied together with x's own.
+__device__ __forceinline__ long long fix_term(double x, int E, int P, uint32_t neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = ((b & 0xfffffffffffffull) | 0x10000000000000ull) << P;
+    const int r = min(E - e, 63);
+    const unsigned long long half = (1ull << r) >> 1;
+    long long v = (long long)((m + half) >> r);
+    v = e ? v : 0ll;
+    return ((uint32_t)(b >> 63) ^ neg) ? -v : v;
 }
 
 template <int MODE>
@@ -38,32 +61,56 @@ __device__ __forceinline__ void hop_acc(double2& acc, uint32_t code, double2 xs,
     }
 }
 
-// H x at element (i_dn, i_up); x already loaded as xv.
-template <int MODE>
-__device__ __forceinline__ double2 hpsi_elem(const SecView& S, const double2* __restrict__ x, int i_dn, int i_up,
-                                             double2 xv, const double2* amp, const double* utab) {
-    const uint32_t bu = __ldg(S.up_bits + i_up), bd = __ldg(S.dn_bits + i_dn);
-    const uint32_t both = bu & bd;
+__device__ __forceinline__ double diag_energy(const SecView& S, int i_dn, int i_up, const double* utab) {
+    const uint32_t both = __ldg(S.up_bits + i_up) & __ldg(S.dn_bits + i_dn);
     double diag = __ldg(S.up_e + i_up) + __ldg(S.dn_e + i_dn);
     for (int c = 0; c < S.nchunk; ++c) diag += utab[c * 256 + ((both >> (8 * c)) & 255u)];
-    double2 hop = make_double2(0.0, 0.0);
+    return diag;
+}
+
+// Hop part of (H x)[i_dn, i_up].  MODE 0-2: FP64 accumulation (MODE 0 without
+// the amplitude, applied by the caller); MODE 3: exact integer accumulation,
+// returned in (ix, iy) as fixed-point sums.
+template <int MODE>
+__device__ __forceinline__ void hop_sum(const SecView& S, const double2* __restrict__ x, int i_dn, int i_up,
+                                        const double2* amp, int E, double2& hop, long long& ix, long long& iy) {
     const double2* row = x + (size_t)i_dn * S.Du;
     const int u0 = __ldg(S.up_off + i_up), u1 = __ldg(S.up_off + i_up + 1);
-#pragma unroll 4
-    for (int e = u0; e < u1; ++e) {
-        const uint2 en = __ldg(S.up_ent + e);
-        hop_acc<MODE>(hop, en.y, row[en.x], amp);
-    }
     const int d0 = __ldg(S.dn_off + i_dn), d1 = __ldg(S.dn_off + i_dn + 1);
+    if (MODE == 3) {
+        const int P = S.fix_pre;
 #pragma unroll 4
-    for (int e = d0; e < d1; ++e) {
-        const uint2 en = __ldg(S.dn_ent + e);
-        hop_acc<MODE>(hop, en.y, x[(size_t)en.x * S.Du + i_up], amp);
+        for (int e = u0; e < u1; ++e) {
+            const uint2 en = __ldg(S.up_ent + e);
+            const double2 xs = row[en.x];
+            ix += fix_term(xs.x, E, P, en.y >> 31);
+            iy += fix_term(xs.y, E, P, en.y >> 31);
+        }
+#pragma unroll 4
+        for (int e = d0; e < d1; ++e) {
+            const uint2 en = __ldg(S.dn_ent + e);
+            const double2 xs = x[(size_t)en.x * S.Du + i_up];
+            ix += fix_term(xs.x, E, P, en.y >> 31);
+            iy += fix_term(xs.y, E, P, en.y >> 31);
+        }
+    } else {
+#pragma unroll 4
+        for (int e = u0; e < u1; ++e) {
+            const uint2 en = __ldg(S.up_ent + e);
+            hop_acc<MODE>(hop, en.y, row[en.x], amp);
+        }
+#pragma unroll 4
+        for (int e = d0; e < d1; ++e) {
+            const uint2 en = __ldg(S.dn_ent + e);
+            hop_acc<MODE>(hop, en.y, x[(size_t)en.x * S.Du + i_up], amp);
+        }
     }
-    if (MODE == 0) {
-        return make_double2(fma(diag, xv.x, S.h0 * hop.x), fma(diag, xv.y, S.h0 * hop.y));
-    }
-    return make_double2(fma(diag, xv.x, hop.x), fma(diag, xv.y, hop.y));
+}
+
+// 2^(E - 1075 - P): value of one unit of the fixed-point sums.
+__device__ __forceinline__ double fix_unit(int E, int P) {
+    const long long ex = (long long)E - 52 - P;  // biased exponent of the unit
+    return ex > 0 ? __longlong_as_double(ex << 52) : 0.0;
 }
 
 __device__ __forceinline__ void stage_tables(const SecView& S, double2* amp, double* utab) {
@@ -72,16 +119,46 @@ __device__ __forceinline__ void stage_tables(const SecView& S, double2* amp, dou
     __syncthreads();
 }
 
+// Largest exponent field over the components of x, into *emax (pre-set to 0).
+__global__ void __launch_bounds__(kThreads) k_maxexp(const double2* __restrict__ x, int d, int* emax) {
+    __shared__ int sm[kThreads / 32];
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        m = max(m, max(exp_field(v.x), exp_field(v.y)));
+    }
+    m = block_max_int(m, sm);
+    if (threadIdx.x == 0) atomicMax(emax, m);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_hpsi(SecView S, const double2* __restrict__ x,
-                                                   double2* __restrict__ y) {
+                                                   double2* __restrict__ y, const int* emax) {
     __shared__ double2 amp[kMaxL * kMaxL];
     __shared__ double utab[4 * 256];
     stage_tables(S, amp, utab);
+    const int E = (MODE == 3) ? *emax : 0;
+    const double unit = (MODE == 3) ? fix_unit(E, S.fix_pre) * S.h0 : 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.d; idx += gridDim.x * blockDim.x) {
         int i_dn, i_up;
         split_index(S, idx, i_dn, i_up);
-        y[idx] = hpsi_elem<MODE>(S, x, i_dn, i_up, x[idx], amp, utab);
+        const double2 xv = x[idx];
+        const double diag = diag_energy(S, i_dn, i_up, utab);
+        double2 hop = make_double2(0.0, 0.0);
+        long long ix = 0, iy = 0;
+        hop_sum<MODE>(S, x, i_dn, i_up, amp, E, hop, ix, iy);
+        double2 r;
+        if (MODE == 3) {
+            r.x = fma(diag, xv.x, unit * __ll2double_rn(ix));
+            r.y = fma(diag, xv.y, unit * __ll2double_rn(iy));
+        } else if (MODE == 0) {
+            r.x = fma(diag, xv.x, S.h0 * hop.x);
+            r.y = fma(diag, xv.y, S.h0 * hop.y);
+        } else {
+            r.x = fma(diag, xv.x, hop.x);
+            r.y = fma(diag, xv.y, hop.y);
+        }
+        y[idx] = r;
     }
 }
 
@@ -91,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_hpsi(SecView S, const double2* __r
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(SecView S, double2* __restrict__ V, size_t colV,
                                                            double2* __restrict__ W, ColScalars* cs, int j,
-                                                           double* part, unsigned* cnt, int nblk) {
+                                                           double* part, unsigned* cnt, int pstride) {
     __shared__ double2 amp[kMaxL * kMaxL];
     __shared__ double utab[4 * 256];
     __shared__ double sm[(kThreads / 32) * 2];
@@ -102,6 +179,9 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(SecView S, double2* _
     stage_tables(S, amp, utab);
     const double sj = C->scale[j];
     const double cprev = (j > 0) ? C->beta[j] * C->scale[j - 1] : 0.0;
+    const int E = (MODE == 3) ? C->emax[j] : 0;
+    const double unit = (MODE == 3) ? fix_unit(E, S.fix_pre) * S.h0 * sj : 0.0;
+    const double hs = S.h0 * sj;
     const double2* x = V + (size_t)b * colV + (size_t)j * S.d;
     const double2* xp = V + (size_t)b * colV + (size_t)(j > 0 ? j - 1 : 0) * S.d;
     double2* w = W + (size_t)b * S.d;
@@ -110,20 +190,29 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(SecView S, double2* _
         int i_dn, i_up;
         split_index(S, idx, i_dn, i_up);
         const double2 xv = x[idx];
-        double2 r = hpsi_elem<MODE>(S, x, i_dn, i_up, xv, amp, utab);
-        r.x *= sj;
-        r.y *= sj;
-        if (j > 0) {
-            const double2 p = xp[idx];
-            r.x = fma(-cprev, p.x, r.x);
-            r.y = fma(-cprev, p.y, r.y);
+        const double sdiag = sj * diag_energy(S, i_dn, i_up, utab);
+        double2 hop = make_double2(0.0, 0.0);
+        long long ix = 0, iy = 0;
+        hop_sum<MODE>(S, x, i_dn, i_up, amp, E, hop, ix, iy);
+        double2 p = make_double2(0.0, 0.0);
+        if (j > 0) p = xp[idx];
+        double2 r;
+        if (MODE == 3) {
+            r.x = fma(sdiag, xv.x, fma(unit, __ll2double_rn(ix), -cprev * p.x));
+            r.y = fma(sdiag, xv.y, fma(unit, __ll2double_rn(iy), -cprev * p.y));
+        } else if (MODE == 0) {
+            r.x = fma(sdiag, xv.x, fma(hs, hop.x, -cprev * p.x));
+            r.y = fma(sdiag, xv.y, fma(hs, hop.y, -cprev * p.y));
+        } else {
+            r.x = fma(sdiag, xv.x, fma(sj, hop.x, -cprev * p.x));
+            r.y = fma(sdiag, xv.y, fma(sj, hop.y, -cprev * p.y));
         }
         w[idx] = r;
         acc[0] = fma(xv.x, r.x, fma(xv.y, r.y, acc[0]));  // Re conj(x) r
     }
     acc[0] *= sj;
     block_sum<2>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part + (size_t)b * nblk * kPart, cnt + b, nblk, red)) {
+    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red)) {
         if (threadIdx.x == 0) {
             const double a = red[0];
             C->alpha[j] = a;
@@ -140,29 +229,43 @@ int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::max(1, std::min((S.d + kThreads - 1) / kThreads, nsm * 8));
-    ProfScope ps("hpsi", st);
-    switch (S.hopmode) {
-        case 0: k_hpsi<0><<<nb, kThreads, 0, st>>>(S, x, y); break;
-        case 1: k_hpsi<1><<<nb, kThreads, 0, st>>>(S, x, y); break;
-        default: k_hpsi<2><<<nb, kThreads, 0, st>>>(S, x, y); break;
+    if (S.hopmode == 0 && S.fix_pre >= 0) {
+        // largest exponent of x first (one extra read of x), then exact hop sums
+        static thread_local int* d_emax = nullptr;
+        if (!d_emax) KG_CUDA(cudaMalloc(&d_emax, sizeof(int)));
+        ProfScope ps("hpsi", st);
+        KG_CUDA(cudaMemsetAsync(d_emax, 0, sizeof(int), st));
+        k_maxexp<<<std::min(nb, nsm * 4), kThreads, 0, st>>>(x, S.d, d_emax);
+        KG_LAUNCHED();
+        k_hpsi<3><<<nb, kThreads, 0, st>>>(S, x, y, d_emax);
+        KG_LAUNCHED();
+        return KG_OK;
     }
+    ProfScope ps("hpsi", st);
+    if (S.hopmode == 0)
+        k_hpsi<0><<<nb, kThreads, 0, st>>>(S, x, y, nullptr);
+    else if (S.hopmode == 1)
+        k_hpsi<1><<<nb, kThreads, 0, st>>>(S, x, y, nullptr);
+    else
+        k_hpsi<2><<<nb, kThreads, 0, st>>>(S, x, y, nullptr);
     KG_LAUNCHED();
     return KG_OK;
 }
 
-int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, cudaStream_t st) {
-    dim3 grid(K.nblk, K.B);
+int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, bool int_hops, cudaStream_t st) {
+    const int mode = S.hopmode == 0 ? ((int_hops && S.fix_pre >= 0) ? 3 : 0) : S.hopmode;
+    const void* kern = mode == 3   ? (const void*)k_lanczos_hpsi<3>
+                       : mode == 0 ? (const void*)k_lanczos_hpsi<0>
+                       : mode == 1 ? (const void*)k_lanczos_hpsi<1>
+                                   : (const void*)k_lanczos_hpsi<2>;
+    dim3 grid(wave_blocks(K, kern), K.B);
+    const int pst = K.nblk * kPart;
     ProfScope ps("lanczos_hpsi", st);
-    switch (S.hopmode) {
-        case 0:
-            k_lanczos_hpsi<0><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, K.nblk);
-            break;
-        case 1:
-            k_lanczos_hpsi<1><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, K.nblk);
-            break;
-        default:
-            k_lanczos_hpsi<2><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, K.nblk);
-            break;
+    switch (mode) {
+        case 3: k_lanczos_hpsi<3><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
+        case 0: k_lanczos_hpsi<0><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
+        case 1: k_lanczos_hpsi<1><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
+        default: k_lanczos_hpsi<2><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
     }
     KG_LAUNCHED();
     return KG_OK;

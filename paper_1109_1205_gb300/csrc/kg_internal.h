@@ -75,6 +75,7 @@ struct SecView {
     int nchunk;
     int hopmode;          // 0: all hops share the real amplitude h0; 1: real; 2: complex
     double h0;
+    int fix_pre;          // P: left pre-shift of fixed-point hop terms (9 - headroom bits)
     uint32_t du_m;        // s / D_up = (umulhi(s, du_m) + s) >> du_l   (s < 2^31)
     int du_l;
 };
@@ -115,6 +116,7 @@ struct ColScalars {
     double scale[kMaxMgs + 1];  // 1/||V_k||: stored Lanczos vectors are unnormalised
     double2 h[kMaxMgs + 1];     // Gram-Schmidt coefficients of the current pass
     double2 c[kMaxMgs];         // combination coefficients (already times scale)
+    int emax[kMaxMgs + 1];      // largest biased FP64 exponent among the components of V_k
     double beta0;               // norm of the start vector
     double lam0, lam1, resest;  // ground-state Ritz value, next one, residual estimate
     double rq, rnorm;           // Rayleigh quotient and residual of a Ritz vector
@@ -129,7 +131,8 @@ struct ColScalars {
 // basis V[b][0..M] of dimension d.
 struct Krylov {
     int B = 0, M = 0, d = 0;
-    int nblk = 1;               // blocks per column of the streaming kernels
+    int nsm = 148;
+    int nblk = 1;               // partial-sum rows per column (>= blocks per column of any launch)
     double2* V = nullptr;       // [B][M+1][d]
     double2* W = nullptr;       // [B][d]
     ColScalars* cs = nullptr;   // [B]
@@ -141,6 +144,8 @@ struct Krylov {
 };
 
 int krylov_alloc(Krylov& K, int B, int M, int d, int nsm);
+// Blocks per column for a one-wave launch of `kern` over the B columns of K.
+int wave_blocks(const Krylov& K, const void* kern, size_t smem = 0);
 void krylov_free(Krylov& K);
 
 // ----------------------------------------------------------- launchers
@@ -148,7 +153,7 @@ void krylov_free(Krylov& K);
 int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st);
 // a2+a3: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
 // partial sums of a_j = <v_j, w> reduced on the device.
-int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, cudaStream_t st);
+int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, bool int_hops, cudaStream_t st);
 // start of a step: beta0 = ||V_0||, scale[0], m_eff = M, status reset.
 int launch_colnorm(Krylov& K, cudaStream_t st);
 // a3 reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or
@@ -189,6 +194,7 @@ struct StepPlan {
     const kg_sector* sec = nullptr;
     Krylov* K = nullptr;
     int reorth = 1;
+    int int_hops = 1;           // exact integer hop sums when the hopping is uniform
     double tau = 0.0;
     const double2* ov = nullptr;
     int n_ov = 0;
@@ -287,28 +293,57 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], int nv, double*
     __syncthreads();
 }
 
-// Deterministic grid reduction.  Each block stores its nv totals (bsum, in
-// shared memory) into its row of part; the last block to arrive (atomic
-// ticket) sums the rows in a fixed order into red (shared, nv doubles),
-// resets the ticket and returns true.  Other blocks return false.
+// Block maximum of an int (valid in thread 0 only).
+__device__ __forceinline__ int block_max_int(int v, int* sm) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int m = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, sm[w]);
+    __syncthreads();
+    return m;
+}
+
+// Biased exponent field of an FP64 value (0 for zero).
+__device__ __forceinline__ int exp_field(double x) {
+    return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
+}
+
+// Deterministic grid reduction over the gridDim.x blocks of one column.
+// Each block stores its nv + nmax totals (bsum, in shared memory) into its
+// row of part; the last block to arrive (atomic ticket) combines the rows in
+// a fixed order into red (shared): values [0, nv) are summed, values
+// [nv, nv + nmax) max-reduced.  It resets the ticket and returns true; other
+// blocks return false.
 __device__ __forceinline__ bool grid_finish(const double* bsum, int nv, double* part, unsigned* cnt,
-                                            int nblk, double* red) {
+                                            int /*unused*/, double* red, int nmax = 0) {
     __shared__ unsigned ticket;
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) part[(size_t)blockIdx.x * kPart + k] = bsum[k];
+    const int nblk = gridDim.x;
+    const int nt = nv + nmax;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) part[(size_t)blockIdx.x * kPart + k] = bsum[k];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);
     __syncthreads();
     if (ticket != (unsigned)(nblk - 1)) return false;
     __threadfence();
-    // value k is summed by one warp: lanes take blocks lane, lane+32, ...
+    // value k is combined by one warp: lanes take blocks lane, lane+32, ...
     // then a fixed shuffle tree -- the order does not depend on timing.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = warp; k < nv; k += nw) {
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)b * kPart + k);
-        s = warp_sum(s);
-        if (lane == 0) red[k] = s;
+    for (int k = warp; k < nt; k += nw) {
+        if (k < nv) {
+            double s = 0.0;
+            for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)b * kPart + k);
+            s = warp_sum(s);
+            if (lane == 0) red[k] = s;
+        } else {
+            double s = 0.0;
+            for (int b = lane; b < nblk; b += 32) s = fmax(s, __ldcg(part + (size_t)b * kPart + k));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+            if (lane == 0) red[k] = s;
+        }
     }
     if (threadIdx.x == 0) *cnt = 0u;
     __syncthreads();

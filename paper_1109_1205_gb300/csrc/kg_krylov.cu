@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "kg_internal.h"
 
@@ -22,9 +24,10 @@ int krylov_alloc(Krylov& K, int B, int M, int d, int nsm) {
     K.B = B;
     K.M = M;
     K.d = d;
-    // about four resident 256-thread blocks per SM in total over all columns
-    const int per_col = std::max(1, (nsm * 4 + B - 1) / B);
-    K.nblk = std::max(1, std::min((d + kThreads - 1) / kThreads, per_col));
+    K.nsm = nsm;
+    // partial-sum rows: enough for a one-wave launch of any kernel (<= 8
+    // resident 256-thread blocks per SM) spread over the B columns
+    K.nblk = std::max(1, std::min((d + kThreads - 1) / kThreads, (nsm * 8 + B - 1) / B));
     const size_t nv = (size_t)B * (M + 1) * (size_t)d;
     KG_CUDA(cudaMalloc(&K.V, sizeof(double2) * nv));
     KG_CUDA(cudaMalloc(&K.W, sizeof(double2) * (size_t)B * d));
@@ -35,6 +38,25 @@ int krylov_alloc(Krylov& K, int B, int M, int d, int nsm) {
     KG_CUDA(cudaMemset(K.cs, 0, sizeof(ColScalars) * B));
     KG_CUDA(cudaMemset(K.cnt, 0, sizeof(unsigned) * B));
     return KG_OK;
+}
+
+int wave_blocks(const Krylov& K, const void* kern, size_t smem) {
+    static std::mutex mu;
+    static std::map<const void*, int> occ;
+    int bps = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = occ.find(kern);
+        if (it == occ.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kThreads, smem) != cudaSuccess || bps < 1)
+                bps = 1;
+            occ[kern] = bps;
+        } else {
+            bps = it->second;
+        }
+    }
+    const int per = std::max(1, (K.nsm * bps) / K.B);
+    return std::max(1, std::min(per, K.nblk));
 }
 
 void krylov_free(Krylov& K) {
@@ -48,24 +70,32 @@ void krylov_free(Krylov& K) {
 }
 
 // ------------------------------------------------- start-of-step norm
+// beta0 = ||V_0||, s_0, the largest exponent of V_0, m_eff = M.
 __global__ void __launch_bounds__(kThreads) k_colnorm(double2* V, size_t colV, int d, ColScalars* cs, int M,
-                                                      double* part, unsigned* cnt, int nblk) {
+                                                      double* part, unsigned* cnt, int pstride) {
     __shared__ double sm[(kThreads / 32) * 2];
+    __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
     const int b = blockIdx.y;
     const double2* x = V + (size_t)b * colV;
     double acc[1] = {0.0};
+    int em = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
         const double2 v = x[i];
         acc[0] = fma(v.x, v.x, fma(v.y, v.y, acc[0]));
+        em = max(em, max(exp_field(v.x), exp_field(v.y)));
     }
+    em = block_max_int(em, smi);
     block_sum<1>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part + (size_t)b * nblk * kPart, cnt + b, nblk, red) && threadIdx.x == 0) {
+    if (threadIdx.x == 0) bs[1] = (double)em;
+    __syncthreads();
+    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red, 1) && threadIdx.x == 0) {
         ColScalars* C = cs + b;
         const double n = sqrt(red[0]);
         C->beta0 = n;
         C->beta[0] = 0.0;
         C->scale[0] = n > 0.0 ? 1.0 / n : 0.0;
+        C->emax[0] = (int)red[1];
         C->m_eff = n > 0.0 ? M : 0;
         C->status = isfinite(n) ? KG_OK : KG_ENUMERIC;
         if (!isfinite(n)) C->m_eff = 0;
@@ -74,7 +104,8 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(double2* V, size_t colV, i
 
 int launch_colnorm(Krylov& K, cudaStream_t st) {
     ProfScope ps("colnorm", st);
-    k_colnorm<<<dim3(K.nblk, K.B), kThreads, 0, st>>>(K.V, K.colV(), K.d, K.cs, K.M, K.part, K.cnt, K.nblk);
+    k_colnorm<<<dim3(wave_blocks(K, (const void*)k_colnorm), K.B), kThreads, 0, st>>>(
+        K.V, K.colV(), K.d, K.cs, K.M, K.part, K.cnt, K.nblk * kPart);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -87,7 +118,7 @@ int launch_colnorm(Krylov& K, cudaStream_t st) {
 template <int NK>
 __global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t colV, const double2* W, int d,
                                                           ColScalars* cs, int j, int k0, int nk, int second,
-                                                          double* part, unsigned* cnt, int nblk) {
+                                                          double* part, unsigned* cnt, int pstride) {
     __shared__ double sm[(kThreads / 32) * 2 * NK];
     __shared__ double bs[2 * NK], red[2 * NK];
     const int b = blockIdx.y;
@@ -117,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t col
         }
     }
     block_sum<2 * NK>(acc, 2 * nk, sm, bs);
-    if (grid_finish(bs, 2 * nk, part + (size_t)b * nblk * kPart, cnt + b, nblk, red)) {
+    if (grid_finish(bs, 2 * nk, part + (size_t)b * pstride, cnt + b, 0, red)) {
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const double s = C->scale[k0 + k];
             C->h[k0 + k] = make_double2(s * red[2 * k], s * red[2 * k + 1]);
@@ -127,9 +158,10 @@ __global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t col
 
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
     ProfScope ps("reorth_dots", st);
-    dim3 g(K.nblk, K.B);
     const int sec = second ? 1 : 0;
-#define KG_DOTS(NK) k_reorth_dots<NK><<<g, kThreads, 0, st>>>(K.V, K.colV(), K.W, K.d, K.cs, j, k0, nk, sec, K.part, K.cnt, K.nblk)
+    const int pst = K.nblk * kPart;
+#define KG_DOTS(NK) k_reorth_dots<NK><<<dim3(wave_blocks(K, (const void*)k_reorth_dots<NK>), K.B), kThreads, 0, st>>>( \
+        K.V, K.colV(), K.W, K.d, K.cs, j, k0, nk, sec, K.part, K.cnt, pst)
     if (nk <= 4) KG_DOTS(4);
     else if (nk <= 8) KG_DOTS(8);
     else if (nk <= 16) KG_DOTS(16);
@@ -157,11 +189,12 @@ constexpr double kSmallCoef = 1e-10;
 
 __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, const double2* W, int d,
                                                      ColScalars* cs, int j, int reorth, int second,
-                                                     double* part, unsigned* cnt, int nblk) {
+                                                     double* part, unsigned* cnt, int pstride) {
     __shared__ double2 coef[kMaxMgs + 1];
     __shared__ float2 coef32[kMaxMgs + 1];
     __shared__ int small[kMaxMgs + 1];
     __shared__ double sm[(kThreads / 32) * 2];
+    __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
     const int b = blockIdx.y;
     ColScalars* C = cs + b;
@@ -183,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
     const double2* vj = Vb + (size_t)j * d;
     double2* out = Vb + (size_t)(j + 1) * d;
     double acc[1] = {0.0};
+    int em = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
         double2 u = w[i];
         if (!second) {
@@ -208,9 +242,14 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
         u.y -= (double)cy;
         out[i] = u;
         acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
+        em = max(em, max(exp_field(u.x), exp_field(u.y)));
     }
+    em = block_max_int(em, smi);
     block_sum<1>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part + (size_t)b * nblk * kPart, cnt + b, nblk, red) && threadIdx.x == 0) {
+    if (threadIdx.x == 0) bs[1] = (double)em;
+    __syncthreads();
+    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red, 1) && threadIdx.x == 0) {
+        C->emax[j + 1] = (int)red[1];
         const double n = sqrt(red[0]);
         double a = C->alpha[j];
         if (reorth) a += C->h[j].x;
@@ -229,8 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
 
 int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
     ProfScope ps("update", st);
-    k_update<<<dim3(K.nblk, K.B), kThreads, 0, st>>>(K.V, K.colV(), K.W, K.d, K.cs, j, reorth ? 1 : 0,
-                                                       second ? 1 : 0, K.part, K.cnt, K.nblk);
+    k_update<<<dim3(wave_blocks(K, (const void*)k_update), K.B), kThreads, 0, st>>>(
+        K.V, K.colV(), K.W, K.d, K.cs, j, reorth ? 1 : 0, second ? 1 : 0, K.part, K.cnt, K.nblk * kPart);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -387,14 +426,16 @@ int launch_tridiag(Krylov& K, int mode, double tau, cudaStream_t st) {
 // ----------------------------------- a5 + a7: combination and overlaps
 // out_b = sum_{k<m} c_k V_k  (Eq. (udelta) in the form V x small vector),
 // then ||out_b|| and <ov_a, out_b> for the n_ov overlap vectors, written to
-// row cs[b].ov_slot of ov_out (the slot advances by one).
+// row cs[b].ov_slot of ov_out (the slot advances by one).  NOV bounds n_ov at
+// compile time so that the accumulators stay in registers.
+template <int NOV>
 __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t colV, int d, ColScalars* cs,
                                                       double2* out, size_t out_stride, const double2* ov,
                                                       int n_ov, size_t ov_stride, double2* ov_out, int ov_rows,
-                                                      double* part, unsigned* cnt, int nblk) {
+                                                      double* part, unsigned* cnt, int pstride) {
     __shared__ double2 coef[kMaxMgs];
-    __shared__ double sm[(kThreads / 32) * (2 * kMaxOv + 2)];
-    __shared__ double bs[2 * kMaxOv + 2], red[2 * kMaxOv + 2];
+    __shared__ double sm[(kThreads / 32) * (2 * NOV + 2)];
+    __shared__ double bs[2 * NOV + 2], red[2 * NOV + 2];
     const int b = blockIdx.y;
     ColScalars* C = cs + b;
     const int m = C->m_eff;
@@ -402,9 +443,9 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
     __syncthreads();
     const double2* Vb = V + (size_t)b * colV;
     double2* o = out + (size_t)b * out_stride;
-    double acc[2 * kMaxOv + 2];
+    double acc[2 * NOV + 2];
 #pragma unroll
-    for (int k = 0; k < 2 * kMaxOv + 2; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 2 * NOV + 2; ++k) acc[k] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
         double2 u = make_double2(0.0, 0.0);
         for (int k = 0; k < m; ++k) {
@@ -416,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
         o[i] = u;
         acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
 #pragma unroll
-        for (int a = 0; a < kMaxOv; ++a) {
+        for (int a = 0; a < NOV; ++a) {
             if (a < n_ov) {
                 const double2 v = ov[(size_t)a * ov_stride + i];
                 acc[2 + 2 * a] = fma(v.x, u.x, fma(v.y, u.y, acc[2 + 2 * a]));
@@ -425,8 +466,8 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
         }
     }
     const int nv = 2 + 2 * n_ov;
-    block_sum<2 * kMaxOv + 2>(acc, nv, sm, bs);
-    if (grid_finish(bs, nv, part + (size_t)b * nblk * kPart, cnt + b, nblk, red)) {
+    block_sum<2 * NOV + 2>(acc, nv, sm, bs);
+    if (grid_finish(bs, nv, part + (size_t)b * pstride, cnt + b, 0, red)) {
         const int slot = C->ov_slot;
         for (int a = threadIdx.x; a < n_ov; a += blockDim.x)
             if (slot < ov_rows) ov_out[((size_t)b * ov_rows + slot) * n_ov + a] = make_double2(red[2 + 2 * a], red[3 + 2 * a]);
@@ -445,8 +486,14 @@ int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov
         return KG_EINVAL;
     }
     ProfScope ps("combine", st);
-    k_combine<<<dim3(K.nblk, K.B), kThreads, 0, st>>>(K.V, K.colV(), K.d, K.cs, out, out_stride, ov, n_ov,
-                                                        ov_stride, ov_out, ov_rows, K.part, K.cnt, K.nblk);
+    const int pst = K.nblk * kPart;
+#define KG_COMB(NOV) k_combine<NOV><<<dim3(wave_blocks(K, (const void*)k_combine<NOV>), K.B), kThreads, 0, st>>>( \
+        K.V, K.colV(), K.d, K.cs, out, out_stride, ov, n_ov, ov_stride, ov_out, ov_rows, K.part, K.cnt, pst)
+    if (n_ov == 0) KG_COMB(0);
+    else if (n_ov <= 4) KG_COMB(4);
+    else if (n_ov <= 12) KG_COMB(12);
+    else KG_COMB(32);
+#undef KG_COMB
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -455,7 +502,7 @@ int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov
 __global__ void __launch_bounds__(kThreads) k_overlaps(const double2* x, size_t x_stride, int d, ColScalars* cs,
                                                        const double2* ov, int n_ov, size_t ov_stride,
                                                        double2* ov_out, int ov_rows, double* part, unsigned* cnt,
-                                                       int nblk) {
+                                                       int pstride) {
     __shared__ double sm[(kThreads / 32) * 2 * kMaxOv];
     __shared__ double bs[2 * kMaxOv], red[2 * kMaxOv];
     const int b = blockIdx.y;
@@ -475,7 +522,7 @@ __global__ void __launch_bounds__(kThreads) k_overlaps(const double2* x, size_t 
         }
     }
     block_sum<2 * kMaxOv>(acc, 2 * n_ov, sm, bs);
-    if (grid_finish(bs, 2 * n_ov, part + (size_t)b * nblk * kPart, cnt + b, nblk, red)) {
+    if (grid_finish(bs, 2 * n_ov, part + (size_t)b * pstride, cnt + b, 0, red)) {
         ColScalars* C = cs + b;
         const int slot = C->ov_slot;
         for (int a = threadIdx.x; a < n_ov; a += blockDim.x)
@@ -492,8 +539,8 @@ int launch_overlaps_cs(Krylov& K, const double2* x, size_t x_stride, const doubl
         return KG_EINVAL;
     }
     ProfScope ps("overlaps", st);
-    k_overlaps<<<dim3(K.nblk, K.B), kThreads, 0, st>>>(x, x_stride, K.d, K.cs, ov, n_ov, ov_stride, ov_out, ov_rows,
-                                                         K.part, K.cnt, K.nblk);
+    k_overlaps<<<dim3(wave_blocks(K, (const void*)k_overlaps), K.B), kThreads, 0, st>>>(
+        x, x_stride, K.d, K.cs, ov, n_ov, ov_stride, ov_out, ov_rows, K.part, K.cnt, K.nblk * kPart);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -516,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
         }
     }
     block_sum<1>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part, cnt, nblk, red) && threadIdx.x == 0) {
+    if (grid_finish(bs, 1, part, cnt, 0, red) && threadIdx.x == 0) {
         if (phase == 0)
             cs->rq = red[0];
         else
@@ -530,7 +577,7 @@ int enqueue_step(const StepPlan& P, cudaStream_t st) {
     const SecView S = P.sec->view();
     KG_TRY(launch_colnorm(K, st));
     for (int j = 0; j < K.M; ++j) {
-        KG_TRY(launch_lanczos_hpsi(S, K, j, st));
+        KG_TRY(launch_lanczos_hpsi(S, K, j, P.int_hops != 0, st));
         if (P.reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));
@@ -573,7 +620,7 @@ int ground_state(kg_sector* s, const kg_opts* o) {
     for (int r = 0; rc == KG_OK && r < o->max_restarts; ++r) {
         if ((rc = launch_colnorm(K, st)) != KG_OK) break;
         for (int j = 0; j < M && rc == KG_OK; ++j) {
-            rc = launch_lanczos_hpsi(S, K, j, st);
+            rc = launch_lanczos_hpsi(S, K, j, o->schedule != 1, st);
             for (int k0 = 0; rc == KG_OK && k0 <= j; k0 += kChunk)
                 rc = launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st);
             if (rc == KG_OK) rc = launch_update(K, j, 1, false, st);

@@ -457,6 +457,13 @@ kg::SecView kg_sector::view() const {
     v.hopmode = hopmode;
     v.h0 = h0;
     {
+        // head room for the exact hop sums: the hops of one element plus one
+        const int maxhops = up.max_row + dn.max_row;
+        int hb = 0;
+        while ((1 << hb) < maxhops + 1) ++hb;
+        v.fix_pre = 9 - hb;  // negative: no integer hop sums for this sector
+    }
+    {
         int l = 0;
         while ((1LL << l) < (long long)Du) ++l;
         v.du_l = l;

@@ -161,6 +161,41 @@ def test_propagate_parity(reorth, dt, n):
     assert abs(np.linalg.norm(y) - 1) < 1e-12
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_hop_sum_schedules(schedule):
+    """Exact integer hop sums (schedule 0) and FP64 hop sums (schedule 1) on
+    uniform-hopping models, through propagation and the ground state."""
+    for model in (W.hubbard_ring(10, 4.0, 5, 4), W.siam_chain(9, 3.0, 4, 5, field=0.7)):
+        s = kg.Sector(model)
+        o = oracle.Sector(model)
+        x = W.random_state(s.dim, 12)
+        xd = dev(x)
+        opts = kg.kg_opts_default(schedule=schedule)
+        s.propagate(xd, -0.05, 10, opts)
+        assert np.max(np.abs(host(xd) - o.propagate(x, -0.5))) < 1e-11
+        E0, _, _ = s.ground_state(opts)
+        e_or, _, _ = o.ground_state()
+        assert abs(E0 - e_or) <= E_TOL * max(1.0, abs(e_or))
+
+
+def test_integer_hop_sums_wide_dynamic_range():
+    """A vector whose components span many decades (and exact zeros) through
+    the exact-sum H*psi: the result must match the oracle component-wise to
+    the precision of the largest component."""
+    m = W.hubbard_ring(8, 2.0, 4, 3)
+    s = kg.Sector(m)
+    o = oracle.Sector(m)
+    rng = np.random.default_rng(3)
+    x = W.random_state(s.dim, 13) * 10.0 ** rng.uniform(-30, 0, s.dim)
+    x[::7] = 0.0
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    s.hpsi(xd, yd, stream())
+    y = host(yd)
+    ref = o.hpsi(x)
+    assert np.max(np.abs(y - ref)) < 1e-15 * np.max(np.abs(x)) * 20
+
+
 def test_propagate_large_sector_and_graphs():
     m = W.hubbard_ring(10, 4.0, 5, 4)
     s = kg.Sector(m)
