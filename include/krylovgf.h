@@ -128,6 +128,19 @@ int kg_neighbour_dim(kg_sector* s, int spin, int dagger, long long* dim);
 int kg_apply_cop(kg_sector* s, int site, int spin, int dagger, const double* x_dev, double* y_dev,
                  void* stream);
 
+/* ---- a7: overlaps of caller-held vectors -----------------------------------
+ * G[b][a] = <x_a | y_b> = sum_i conj(x_a[i]) y_b[i] for the n_x vectors
+ * X_dev (complex, [n_x][d] row-major) and the n_y vectors Y_dev ([n_y][d]):
+ * the inner products from which the Green's functions are assembled
+ * (Section 3, Eq. (psigreen); Section 4, step (iv)).  G_dev: device,
+ * complex [n_y][n_x].  Limits: 1 <= n_x <= 32, n_y >= 1, 1 <= d < 2^31.
+ * The reduction is deterministic (fixed order for a given device and size).
+ * Partial sums live in a library-owned, grow-only scratch buffer per device
+ * (allocated on first use), so calls must not run concurrently on one
+ * device.  stream as for kg_hpsi.  Asynchronous. */
+int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
+                void* stream);
+
 /* ---- a3-a5: ground state -------------------------------------------------
  * Lanczos ground state of the sector (Section 2: recursion Eq. (recursion)
  * with full reorthogonalisation, T of Eq. (tmatrix) diagonalised on the

@@ -57,6 +57,7 @@ _sig = {
     "kg_hpsi": (_I, [_P, _P, _P, _P]),
     "kg_neighbour_dim": (_I, [_P, _I, _I, ctypes.POINTER(_LL)]),
     "kg_apply_cop": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "kg_overlaps": (_I, [_P, _I, _P, _I, _LL, _P, _P]),
     "kg_ground_state": (_I, [_P, ctypes.POINTER(Opts), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)]),
     "kg_copy_ground_state": (_I, [_P, _P, _I]),
@@ -168,6 +169,12 @@ def kg_neighbour_dim(handle, spin, dagger):
 def kg_apply_cop(handle, site, spin, dagger, x_dev, y_dev, stream=None):
     _check(lib.kg_apply_cop(handle, site, spin, 1 if dagger else 0, _addr(x_dev), _addr(y_dev), _stream(stream)),
            "kg_apply_cop")
+
+
+def kg_overlaps(X_dev, n_x, Y_dev, n_y, d, G_dev, stream=None):
+    """G[b][a] = <x_a|y_b> on the device (complex [n_y][n_x])."""
+    _check(lib.kg_overlaps(_addr(X_dev), int(n_x), _addr(Y_dev), int(n_y), int(d), _addr(G_dev), _stream(stream)),
+           "kg_overlaps")
 
 
 def kg_ground_state(handle, opts=None):

@@ -122,6 +122,32 @@ def test_cop_missing_neighbour_is_einval():
         s.neighbour_dim(1, False)  # N_dn = 0: nothing to annihilate
 
 
+# ------------------------------------------------------- a7 overlaps
+@pytest.mark.parametrize("n_x,n_y,d", [(1, 1, 1), (3, 5, 1000), (12, 12, 731808), (32, 40, 4097), (17, 1, 300001)])
+def test_overlaps_parity(n_x, n_y, d):
+    rng = np.random.default_rng(n_x * 1000 + n_y)
+    X = rng.standard_normal((n_x, d)) + 1j * rng.standard_normal((n_x, d))
+    Y = rng.standard_normal((n_y, d)) + 1j * rng.standard_normal((n_y, d))
+    G = torch.empty((n_y, n_x), dtype=torch.complex128, device="cuda")
+    Xd, Yd = dev(X), dev(Y)
+    kg.kg_overlaps(Xd, n_x, Yd, n_y, d, G, stream())
+    ref = np.conj(X) @ Y.T  # ref[a, b] = <x_a | y_b>
+    got = host(G)
+    assert np.max(np.abs(got - ref.T)) < 1e-12 * max(1.0, np.sqrt(d))
+    # deterministic: a second call gives the same bits
+    G2 = torch.empty_like(G)
+    kg.kg_overlaps(Xd, n_x, Yd, n_y, d, G2, stream())
+    assert np.array_equal(host(G2), got)
+
+
+def test_overlaps_rejects_bad_sizes():
+    x = torch.zeros(8, dtype=torch.complex128, device="cuda")
+    for n_x, n_y, d in ((0, 1, 8), (33, 1, 8), (1, 0, 8), (1, 1, 0)):
+        with pytest.raises(kg.KGError) as e:
+            kg.kg_overlaps(x, n_x, x, n_y, d, x, stream())
+        assert e.value.code == kg.KG_EINVAL
+
+
 # ---------------------------------------------------------- a3-a5 ground state
 GS_MODELS = [
     ("c1", W.config_c1()["model"]),
