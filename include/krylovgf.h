@@ -141,6 +141,20 @@ int kg_apply_cop(kg_sector* s, int site, int spin, int dagger, const double* x_d
 int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
                 void* stream);
 
+/* The same overlaps for callers that cannot allocate device memory at call
+ * time: inside CUDA stream capture, under a fixed device-memory budget or a
+ * pool that must not grow, or where the allocator's implicit synchronisation
+ * is not acceptable.  The paper has no counterpart; this is a deployment
+ * variant.  It allocates nothing: its scratch is a fixed 1.2 MB array in the
+ * library's device image (every GPU that loads the library holds it until the
+ * process exits).  Limits as for kg_overlaps plus n_y <= 64; larger n_y is
+ * rejected with KG_EINVAL.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * All calls share the scratch: calls that overlap on the GPU race, so issue
+ * them on one stream or otherwise order them. */
+int kg_overlaps_noalloc(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
+                        void* stream);
+
 /* ---- a3-a5: ground state -------------------------------------------------
  * Lanczos ground state of the sector (Section 2: recursion Eq. (recursion)
  * with full reorthogonalisation, T of Eq. (tmatrix) diagonalised on the

@@ -122,3 +122,68 @@ extern "C" int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, in
     return launch_inner(reinterpret_cast<const double2*>(X_dev), n_x, reinterpret_cast<const double2*>(Y_dev), n_y,
                         (int)d, per_col, s->part, s->cnt, reinterpret_cast<double2*>(G_dev), (cudaStream_t)stream);
 }
+
+// ------------------------------------------- no-allocation variant
+// Some callers cannot allocate device memory at call time: code running while
+// a stream is being captured into a CUDA graph, code under a fixed device
+// memory budget or a pool that must not grow, and code that must not hit the
+// allocator's implicit synchronisation.  kg_overlaps_noalloc serves them with
+// the same kernel as kg_overlaps, its partial sums and tickets held in fixed
+// arrays of this library's device image instead of allocated memory.
+namespace kg {
+
+constexpr int kNoAllocCols = 64;    // largest n_y accepted
+constexpr int kNoAllocRows = 2048;  // partial-sum rows of kPart doubles (1,179,648 bytes)
+
+static __device__ __align__(256) double g_noalloc_part[kNoAllocRows * kPart];
+static __device__ __align__(256) unsigned g_noalloc_cnt[kNoAllocCols];
+
+// Device addresses of the arrays on one device.  In host code the symbols are
+// host-side stand-ins, so the addresses come from cudaGetSymbolAddress, once
+// per device, with that device current.
+struct NoAllocPtrs {
+    double* part = nullptr;
+    unsigned* cnt = nullptr;
+};
+
+static int noalloc_ptrs(NoAllocPtrs* out) {
+    static std::mutex mu;
+    static std::map<int, NoAllocPtrs> cache;
+    int dev = 0;
+    KG_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it == cache.end()) {
+        NoAllocPtrs p;
+        KG_CUDA(cudaGetSymbolAddress((void**)&p.part, g_noalloc_part));
+        KG_CUDA(cudaGetSymbolAddress((void**)&p.cnt, g_noalloc_cnt));
+        it = cache.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return KG_OK;
+}
+
+// The tickets must start at zero; device code names the array directly.
+__global__ void k_noalloc_clear() {
+    for (int i = threadIdx.x; i < kNoAllocCols; i += blockDim.x) g_noalloc_cnt[i] = 0u;
+}
+
+}  // namespace kg
+
+extern "C" int kg_overlaps_noalloc(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d,
+                                   double* G_dev, void* stream) {
+    using namespace kg;
+    KG_TRY(check_inner_args(X_dev, n_x, Y_dev, n_y, d, G_dev));
+    if (n_y > kNoAllocCols) {
+        set_error("kg_overlaps_noalloc: n_y = %d exceeds its fixed scratch limit of %d columns", n_y, kNoAllocCols);
+        return KG_EINVAL;
+    }
+    NoAllocPtrs p;
+    KG_TRY(noalloc_ptrs(&p));
+    const int per_col = std::min(blocks_per_column(n_y, d), kNoAllocRows / n_y);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_noalloc_clear<<<1, kNoAllocCols, 0, st>>>();
+    KG_LAUNCHED();
+    return launch_inner(reinterpret_cast<const double2*>(X_dev), n_x, reinterpret_cast<const double2*>(Y_dev), n_y,
+                        (int)d, per_col, p.part, p.cnt, reinterpret_cast<double2*>(G_dev), st);
+}
