@@ -247,12 +247,16 @@ def run_ours(args):
     dk = kernels[dom]
     hbm_frac = dk.get("gbs", 0.0) / peaks["hbm_gbs"]
     fp_frac = dk.get("tflops_fp64", 0.0) / fp64
+    # DRAM traffic of the dominant kernel: the traffic/algorithmic ratio of an
+    # ncu capture (profiles/traffic.json) times this launch's algorithmic bytes,
+    # null once the kernel sources differ from the captured ones.
     traffic = None
     tj = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tj):
+    if os.path.exists(tj) and dom in by:
         rec = json.load(open(tj)).get(dom)
         if rec and rec.get("source_hash") == source_hash(rec.get("sources", [])):
-            traffic = rec.get("bytes_per_launch")
+            per_launch = by[dom] * n_prof_steps / max(1, prof[dom][0])
+            traffic = round(rec["ratio"] * per_launch)
     if hbm_frac >= fp_frac:
         roof = {"bound": "hbm", "achieved": dk.get("gbs"), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": dom,
@@ -364,6 +368,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_ncu_case(args):
+    """Small case for full ncu captures: one column of the c2 N-1 sector
+    (d = 731,808, 0.26 GB of Krylov basis, more than the L2) propagated
+    backward by 3 Krylov steps with the benchmark's options."""
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c2()
+    sec = kg.Sector(W.with_sector(cfg["fin"], 5, 6))
+    x = torch.from_numpy(W.random_state(sec.dim, 5)).cuda()
+    sec.propagate(x, -cfg["dt"], 3, kg.kg_opts_default(M=cfg["M"], reorth=1))
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "c2 N-1 column", "d": sec.dim, "launches": kg.kg_launch_count(),
+                      "norm": float(torch.linalg.vector_norm(x).item())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +394,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-gsteps", type=int, default=4)
+    ap.add_argument("--ncu-case", action="store_true", help="small case for full ncu captures")
     args = ap.parse_args()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
