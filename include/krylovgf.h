@@ -190,6 +190,22 @@ int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_o
 int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps,
                          const kg_opts* o, double* G_gtr, double* G_les);
 
+/* ---- a9: batched equilibrium Green's functions ----------------------------
+ * The equilibrium Green's functions of n_inst independent sectors (for
+ * example the repeated impurity solves of DMFT/VCA-type embedding schemes,
+ * Section 1), computed together: after each instance's ground state, the
+ * columns of all instances -- of different dimensions -- are propagated in
+ * the same launches (one CUDA graph per time step, work lists sized to fill
+ * the GPU, a work-list scale chosen by a short timing run).  Same orbitals,
+ * dt and n_steps for all instances.
+ *   G_gtr, G_les: host, complex [n_inst][n_steps+1][n_orb][n_orb];
+ *   status: host int[n_inst] (may be NULL): KG_OK, or the error of that
+ *           instance's ground state (KG_ENOCONV, KG_EDEGEN, ...) or
+ *           KG_ENUMERIC; the G of a failed instance is left zero.
+ * Returns KG_OK unless an argument is invalid or the device fails. */
+int kg_green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt,
+                                 int n_steps, const kg_opts* o, double* G_gtr, double* G_les, int* status);
+
 /* ---- a8: nonequilibrium (Keldysh) Green's function -----------------------
  * Section 4, steps (i)-(iv): |0> = ground state of H_ini; Phi(t) =
  * e^{-iH t}|0> with H = H_fin; Psi_a(t) = e^{iHt} c_a Phi(t) and

@@ -64,6 +64,7 @@ _sig = {
     "kg_propagate": (_I, [_P, _P, _D, _I, ctypes.POINTER(Opts)]),
     "kg_green_equilibrium": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_keldysh": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P]),
+    "kg_green_equilibrium_batched": (_I, [_P, _I, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -204,6 +205,22 @@ def kg_green_equilibrium(handle, orbitals, dt, n_steps, opts=None):
     _check(lib.kg_green_equilibrium(handle, orb.ctypes.data, n, float(dt), int(n_steps), ctypes.byref(o),
                                     Gg.ctypes.data, Gl.ctypes.data), "kg_green_equilibrium")
     return Gg, Gl
+
+
+def kg_green_equilibrium_batched(handles, orbitals, dt, n_steps, opts=None):
+    """Equilibrium G of many sectors in one batch; returns (G_gtr, G_les, status)
+    with G of shape [n_inst, n_steps+1, n_orb, n_orb]."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    arr = (_P * len(handles))(*handles)
+    Gg = np.zeros((len(handles), n_steps + 1, n, n), dtype=np.complex128)
+    Gl = np.zeros_like(Gg)
+    status = np.zeros(len(handles), dtype=np.int32)
+    _check(lib.kg_green_equilibrium_batched(ctypes.cast(arr, _P), len(handles), orb.ctypes.data, n, float(dt),
+                                            int(n_steps), ctypes.byref(o), Gg.ctypes.data, Gl.ctypes.data,
+                                            status.ctypes.data), "kg_green_equilibrium_batched")
+    return Gg, Gl, status
 
 
 def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):

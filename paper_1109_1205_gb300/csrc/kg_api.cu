@@ -22,56 +22,32 @@ int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o
     cudaStream_t st = pick_stream(s, o);
     const int d = (int)s->d;
     Krylov K;
-    int rc = krylov_alloc(K, 1, std::min(o->M, d), d, s->nsm);
-    StepPlan P;
-    P.sec = s;
-    P.K = &K;
-    P.reorth = o->reorth;
-    P.int_hops = o->schedule != 1;
-    P.tau = dt;
-    if (rc == KG_OK)
-        rc = cudaMemcpyAsync(K.V, x, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-    if (o->use_graphs && n_steps > 1 && !profiling()) {
-        // one graph for the repeated step
-        struct Local {
-            cudaGraphExec_t exec = nullptr;
-            ~Local() {
-                if (exec) cudaGraphExecDestroy(exec);
-            }
-        } L;
-        cudaGraph_t g = nullptr;
-        size_t nodes = 0;
-        if (rc == KG_OK) rc = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? KG_OK : KG_ECUDA;
-        if (rc == KG_OK) {
-            set_capturing(true);
-            const int r2 = enqueue_step(P, st);
-            set_capturing(false);
-            const cudaError_t e = cudaStreamEndCapture(st, &g);
-            rc = r2 != KG_OK ? r2 : (e == cudaSuccess ? KG_OK : cuda_fail(e, "capture", __FILE__, __LINE__));
-        }
-        if (rc == KG_OK) {
-            cudaGraphGetNodes(g, nullptr, &nodes);
-            rc = cudaGraphInstantiate(&L.exec, g, 0) == cudaSuccess ? KG_OK : KG_ECUDA;
-        }
-        if (g) cudaGraphDestroy(g);
-        for (int n = 0; rc == KG_OK && n < n_steps; ++n) {
-            rc = cudaGraphLaunch(L.exec, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-            count_launch(nodes);
-        }
-        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
-    } else {
-        for (int n = 0; rc == KG_OK && n < n_steps; ++n) rc = enqueue_step(P, st);
+    StepRunner R;
+    int rc = krylov_alloc(K, {s}, std::min(o->M, d), s->nsm, o->schedule != 1);
+    if (rc == KG_OK) {
+        K.hdesc[0].tau = dt;
+        rc = krylov_upload(K, st);
     }
+    if (rc == KG_OK)
+        rc = cudaMemcpyAsync(K.vec(0, 0), x, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                 ? KG_OK
+                 : KG_ECUDA;
+    if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0 && n_steps > 1);
+    for (int n = 0; rc == KG_OK && n < n_steps; ++n) rc = R.run(st);
     ColScalars h;
     if (rc == KG_OK)
-        rc = cudaMemcpyAsync(x, K.V, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        rc = cudaMemcpyAsync(x, K.vec(0, 0), sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                 ? KG_OK
+                 : KG_ECUDA;
     if (rc == KG_OK)
         rc = cudaMemcpyAsync(&h, K.cs, sizeof(ColScalars), cudaMemcpyDeviceToHost, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-    if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : cuda_fail(cudaGetLastError(), "propagate", __FILE__, __LINE__);
+    if (rc == KG_OK)
+        rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : cuda_fail(cudaGetLastError(), "propagate", __FILE__, __LINE__);
     if (rc == KG_OK && h.status == KG_ENUMERIC) {
         set_error("non-finite value during propagation");
         rc = KG_ENUMERIC;
     }
+    R.release();
     krylov_free(K);
     return rc;
 }
@@ -205,6 +181,13 @@ int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int
     }
     kg_opts tmp;
     return green_equilibrium(s, orb, n_orb, dt, n_steps, opts_or_default(o, &tmp), G_gtr, G_les);
+}
+
+int kg_green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
+                                 const kg_opts* o, double* G_gtr, double* G_les, int* status) {
+    kg_opts tmp;
+    return green_equilibrium_batched(s, n_inst, orb, n_orb, dt, n_steps, opts_or_default(o, &tmp), G_gtr, G_les,
+                                     status);
 }
 
 int kg_green_keldysh(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,

@@ -1,10 +1,11 @@
-// kg_green.cu -- a7/a8: the Green's-function drivers.
+// kg_green.cu -- a7/a8/a9: the Green's-function drivers.
 //
 // Equilibrium (Section 3, Eqs. (psit), (psigreen), eta = 0; hole part after
 // Eq. (gomega)):  the columns c^dag_a'|0> (particle) and c_a|0> (hole) are
 // propagated together, one batched Krylov step per time step, and their
 // overlaps with the fixed vectors c^dag_a|0> / c_a'|0> are fused into the
-// combination pass of every step.
+// combination pass of every step.  The batched form runs the columns of many
+// instances (different sectors and dimensions) in the same launches.
 //
 // Nonequilibrium (Section 4, steps (i)-(iv)): Phi(t_k) = e^{-iHt_k}|0> is
 // stored for every grid time; row k of step (iii) starts the columns
@@ -20,57 +21,42 @@
 
 namespace kg {
 
-int launch_overlaps_cs(Krylov& K, const double2* x, size_t x_stride, const double2* ov, int n_ov,
-                       size_t ov_stride, double2* ov_out, int ov_rows, cudaStream_t st);
-
-// Replays the launch sequence of one propagation step, as a CUDA graph when
-// allowed (the sequence is fixed: iteration counts and early exits after a
-// breakdown are decided on the device).
-struct StepRunner {
-    StepPlan plan;
-    cudaGraphExec_t exec = nullptr;
-    size_t nodes = 0;
-    bool graph = false;
-
-    int init(const StepPlan& P, cudaStream_t st, bool use_graph) {
-        plan = P;
-        graph = false;
-        if (!use_graph || profiling()) return KG_OK;
-        cudaGraph_t g = nullptr;
-        KG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        set_capturing(true);
-        const int rc = enqueue_step(P, st);
-        set_capturing(false);
-        const cudaError_t e = cudaStreamEndCapture(st, &g);
-        if (rc != KG_OK) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
-        cudaGraphGetNodes(g, nullptr, &nodes);
-        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
-        graph = true;
-        return KG_OK;
+int StepRunner::init(Krylov& k, int reorth_mode, cudaStream_t st, bool use_graph) {
+    release();
+    K = &k;
+    reorth = reorth_mode;
+    KG_TRY(prepare_step(k, reorth));
+    if (!use_graph || profiling()) return KG_OK;
+    cudaGraph_t g = nullptr;
+    KG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    const int rc = enqueue_step(*K, reorth, st);
+    set_capturing(false);
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != KG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
     }
-    int run(cudaStream_t st) {
-        if (!graph || profiling()) return enqueue_step(plan, st);
-        KG_CUDA(cudaGraphLaunch(exec, st));
-        count_launch(nodes);
-        return KG_OK;
-    }
-    void release() {
-        if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        graph = false;
-    }
-};
-
-static int reset_slots(Krylov& K, cudaStream_t st) {
-    // ov_slot of every column back to 0 (one int per ColScalars record)
-    KG_CUDA(cudaMemset2DAsync(&K.cs->ov_slot, sizeof(ColScalars), 0, sizeof(int), K.B, st));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+    graph = true;
     return KG_OK;
+}
+
+int StepRunner::run(cudaStream_t st) {
+    if (!graph || profiling()) return enqueue_step(*K, reorth, st);
+    KG_CUDA(cudaGraphLaunch(exec, st));
+    count_launch(nodes);
+    return KG_OK;
+}
+
+void StepRunner::release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    graph = false;
 }
 
 static int ensure_gs(kg_sector* s, const kg_opts* o) {
@@ -116,99 +102,235 @@ static int check_opts(const kg_opts* o) {
 }
 
 // ------------------------------------------------------------ equilibrium
-int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
-                      double* G_gtr, double* G_les) {
-    KG_TRY(check_orbitals(s, orb, n_orb));
-    KG_TRY(check_opts(o));
-    if (n_steps < 0 || !G_gtr || !G_les) {
-        set_error("bad n_steps or NULL output");
-        return KG_EINVAL;
-    }
-    KG_TRY(ensure_gs(s, o));
-    cudaStream_t st = pick_stream(s, o);
-    const size_t per_t = (size_t)n_orb * n_orb * 2;
-    std::memset(G_gtr, 0, sizeof(double) * per_t * (n_steps + 1));
-    std::memset(G_les, 0, sizeof(double) * per_t * (n_steps + 1));
+// One (instance, spin, kind) group of columns: the na start vectors
+// c^dag_p|0> (kind 1, forward in time) or c_p|0> (kind 0, backward) in the
+// neighbour sector, which are also the overlap partners of every step.
+struct EqGroup {
+    int inst = 0, spin = 0, dagger = 0;
+    std::vector<int> idx;      // orbital indices of this spin
+    kg_sector* nb = nullptr;
+    double2* chi = nullptr;    // [na][dn]
+    int col0 = 0;              // first column of the group in the batch
+    size_t ov0 = 0;            // first overlap entry of the group
+};
+
+static void eq_groups(std::vector<EqGroup>& out, std::vector<const kg_sector*>& cols, kg_sector* s, int inst,
+                      const int* orb, int n_orb) {
     std::vector<int> idx[2];
     groups(orb, n_orb, idx);
-    const int rows = n_steps + 1;
     for (int spin = 0; spin < 2; ++spin) {
-        const int na = (int)idx[spin].size();
-        if (!na) continue;
+        if (idx[spin].empty()) continue;
         for (int dagger = 1; dagger >= 0; --dagger) {
             kg_sector* nb = nullptr;
-            if (neighbour(s, spin, dagger, &nb) != KG_OK) continue;  // empty/full: G part is zero
-            const int dn = (int)nb->d;
-            Krylov K;
-            double2 *chi = nullptr, *ov = nullptr;
-            StepRunner R;
-            int rc = krylov_alloc(K, na, std::min(o->M, dn), dn, s->nsm);
-            if (rc == KG_OK && cudaMalloc(&chi, sizeof(double2) * (size_t)na * dn) != cudaSuccess) rc = KG_ENOMEM;
-            if (rc == KG_OK && cudaMalloc(&ov, sizeof(double2) * (size_t)na * rows * na) != cudaSuccess) rc = KG_ENOMEM;
-            for (int a = 0; rc == KG_OK && a < na; ++a)
-                rc = launch_cop(s, nb, orb[2 * idx[spin][a]], spin, dagger, s->gs, chi + (size_t)a * dn, st);
-            if (rc == KG_OK)
-                rc = cudaMemcpy2DAsync(K.V, K.colV() * sizeof(double2), chi, (size_t)dn * sizeof(double2),
-                                       (size_t)dn * sizeof(double2), na, cudaMemcpyDeviceToDevice, st) == cudaSuccess
-                         ? KG_OK
-                         : KG_ECUDA;
-            if (rc == KG_OK) rc = reset_slots(K, st);
-            if (rc == KG_OK) rc = launch_overlaps_cs(K, K.V, K.colV(), chi, na, dn, ov, rows, st);
-            StepPlan P;
-            P.sec = nb;
-            P.K = &K;
-            P.reorth = o->reorth;
-            P.int_hops = o->schedule != 1;
-            P.tau = dagger ? dt : -dt;  // particle: e^{-iHt}; hole: e^{+iHt}
-            P.ov = chi;
-            P.n_ov = na;
-            P.ov_stride = dn;
-            P.ov_out = ov;
-            P.ov_rows = rows;
-            if (rc == KG_OK && n_steps > 0) rc = R.init(P, st, o->use_graphs != 0);
-            for (int k = 1; rc == KG_OK && k <= n_steps; ++k) rc = R.run(st);
-            std::vector<double2> hov((size_t)na * rows * na);
-            if (rc == KG_OK &&
-                (cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * hov.size(), cudaMemcpyDeviceToHost, st) !=
-                     cudaSuccess ||
-                 cudaStreamSynchronize(st) != cudaSuccess))
-                rc = cuda_fail(cudaGetLastError(), "overlap readback", __FILE__, __LINE__);
-            int status = KG_OK;
-            if (rc == KG_OK) {
-                std::vector<ColScalars> hcs(na);
-                cudaMemcpy(hcs.data(), K.cs, sizeof(ColScalars) * na, cudaMemcpyDeviceToHost);
-                for (auto& c : hcs)
-                    if (c.status == KG_ENUMERIC) status = KG_ENUMERIC;
-            }
-            R.release();
-            krylov_free(K);
-            cudaFree(chi);
-            cudaFree(ov);
-            if (rc != KG_OK) return rc;
-            if (status != KG_OK) {
-                set_error("non-finite value during propagation");
-                return status;
-            }
-            // assemble: ov[b][k][a] = <vec_a | propagated vec_b at t_k>
-            for (int k = 0; k < rows; ++k) {
-                const double t = dt * k;
-                const std::complex<double> ph = dagger ? std::complex<double>(0.0, -1.0) * std::exp(std::complex<double>(0.0, s->E0 * t))
-                                                       : std::complex<double>(0.0, 1.0) * std::exp(std::complex<double>(0.0, -s->E0 * t));
-                for (int bcol = 0; bcol < na; ++bcol)
-                    for (int a = 0; a < na; ++a) {
-                        const double2 v = hov[((size_t)bcol * rows + k) * na + a];
-                        const std::complex<double> g = ph * std::complex<double>(v.x, v.y);
-                        // particle: G^>_{a, b}; hole: G^<_{b, a}
-                        const int r = dagger ? idx[spin][a] : idx[spin][bcol];
-                        const int c = dagger ? idx[spin][bcol] : idx[spin][a];
-                        double* G = dagger ? G_gtr : G_les;
-                        G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2] = g.real();
-                        G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2 + 1] = g.imag();
-                    }
-            }
+            if (neighbour(s, spin, dagger, &nb) != KG_OK) continue;  // empty/full band: that part is zero
+            EqGroup g;
+            g.inst = inst;
+            g.spin = spin;
+            g.dagger = dagger;
+            g.idx = idx[spin];
+            g.nb = nb;
+            g.col0 = (int)cols.size();
+            for (size_t a = 0; a < g.idx.size(); ++a) cols.push_back(nb);
+            out.push_back(g);
         }
     }
-    return KG_OK;
+}
+
+// Builds the start vectors, propagates every column of the batch n_steps
+// times and leaves the raw overlaps in ov: group g's column a has its rows
+// [rows][na] at g.ov0 + a*rows*na.  With `tune`, the work-list scale is first
+// chosen by timing two steps per candidate (the autotuner).
+static int eq_run(std::vector<EqGroup>& G, const std::vector<kg_sector*>& inst, const int* orb, Krylov& K,
+                  double2* ov, int rows, double dt, int n_steps, const kg_opts* o, bool tune, cudaStream_t st) {
+    size_t off = 0;
+    for (auto& g : G) {
+        const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+        kg_sector* s = inst[g.inst];
+        for (int a = 0; a < na; ++a)
+            KG_TRY(launch_cop(s, g.nb, orb[2 * g.idx[a]], g.spin, g.dagger, s->gs, g.chi + (size_t)a * dn, st));
+        g.ov0 = off;
+        for (int a = 0; a < na; ++a) {
+            ColDesc& D = K.hdesc[g.col0 + a];
+            D.tau = g.dagger ? dt : -dt;  // particle: e^{-iHt}; hole: e^{+iHt}
+            D.ov = g.chi;
+            D.n_ov = na;
+            D.ov_stride = dn;
+            D.ov_out = ov + off;
+            D.ov_rows = rows;
+            off += (size_t)rows * na;
+        }
+    }
+    KG_TRY(krylov_upload(K, st));
+    // row 0 (t = 0): <chi_a | chi_b> of every group
+    for (auto& g : G) {
+        const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+        KG_TRY(launch_inner_lib(g.chi, na, g.chi, na, dn, ov + g.ov0, rows * na, st));
+    }
+    auto load_start = [&]() -> int {
+        for (auto& g : G) {
+            const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+            for (int a = 0; a < na; ++a)
+                KG_CUDA(cudaMemcpyAsync(K.vec(g.col0 + a, 0), g.chi + (size_t)a * dn, sizeof(double2) * dn,
+                                        cudaMemcpyDeviceToDevice, st));
+        }
+        return launch_set_slots(K, 1, st);
+    };
+    if (n_steps == 0) return KG_OK;
+    StepRunner R;
+    const bool graphs = o->use_graphs != 0;
+    if (tune && n_steps > 4 && graphs && !profiling()) {
+        // autotuner: work-list size relative to one wave, timed on two steps
+        const double cands[3] = {0.5, 1.0, 2.0};
+        double best_t = 1e300, best = 1.0;
+        cudaEvent_t e0, e1;
+        KG_CUDA(cudaEventCreate(&e0));
+        KG_CUDA(cudaEventCreate(&e1));
+        for (double c : cands) {
+            K.wave_scale = c;
+            KG_TRY(load_start());
+            KG_TRY(R.init(K, o->reorth, st, true));
+            KG_TRY(R.run(st));
+            cudaEventRecord(e0, st);
+            KG_TRY(R.run(st));
+            KG_TRY(R.run(st));
+            cudaEventRecord(e1, st);
+            KG_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        K.wave_scale = best;
+    }
+    KG_TRY(load_start());
+    int rc = R.init(K, o->reorth, st, graphs);
+    for (int k = 1; rc == KG_OK && k <= n_steps; ++k) rc = R.run(st);
+    R.release();
+    return rc;
+}
+
+// G entries of one instance from the raw overlaps (host): ov[b][k][a] =
+// <vec_a | propagated vec_b at t_k>; particle gives G^>_{a b}, hole G^<_{b a}.
+static void eq_assemble(const EqGroup& g, const std::vector<double2>& hov, int rows, double dt, double E0, int n_orb,
+                        double* G_gtr, double* G_les) {
+    const int na = (int)g.idx.size();
+    for (int k = 0; k < rows; ++k) {
+        const double t = dt * k;
+        const std::complex<double> ph = g.dagger ? std::complex<double>(0.0, -1.0) * std::exp(std::complex<double>(0.0, E0 * t))
+                                                 : std::complex<double>(0.0, 1.0) * std::exp(std::complex<double>(0.0, -E0 * t));
+        for (int bcol = 0; bcol < na; ++bcol)
+            for (int a = 0; a < na; ++a) {
+                const double2 v = hov[g.ov0 + ((size_t)bcol * rows + k) * na + a];
+                const std::complex<double> val = ph * std::complex<double>(v.x, v.y);
+                const int r = g.dagger ? g.idx[a] : g.idx[bcol];
+                const int c = g.dagger ? g.idx[bcol] : g.idx[a];
+                double* G = g.dagger ? G_gtr : G_les;
+                G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2] = val.real();
+                G[((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2 + 1] = val.imag();
+            }
+    }
+}
+
+// Equilibrium G of n_inst sectors (one instance when n_inst = 1), every
+// column of every instance in one batch.  status[i] receives the ground-state
+// status of instance i (its G stays zero unless KG_OK).
+static int green_eq_batch(kg_sector* const* sv, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
+                          const kg_opts* o, double* G_gtr, double* G_les, int* status, bool tune) {
+    KG_TRY(check_opts(o));
+    if (n_steps < 0 || !G_gtr || !G_les || n_inst < 1) {
+        set_error("bad n_steps, n_inst or NULL output");
+        return KG_EINVAL;
+    }
+    for (int i = 0; i < n_inst; ++i) {
+        if (!sv[i]) {
+            set_error("NULL sector %d", i);
+            return KG_EINVAL;
+        }
+        KG_TRY(check_orbitals(sv[i], orb, n_orb));
+    }
+    const int rows = n_steps + 1;
+    const size_t per_inst = (size_t)rows * n_orb * n_orb * 2;
+    std::memset(G_gtr, 0, sizeof(double) * per_inst * n_inst);
+    std::memset(G_les, 0, sizeof(double) * per_inst * n_inst);
+    std::vector<kg_sector*> inst(sv, sv + n_inst);
+    std::vector<EqGroup> G;
+    std::vector<const kg_sector*> cols;
+    int first_err = KG_OK;
+    for (int i = 0; i < n_inst; ++i) {
+        const int r = ensure_gs(inst[i], o);
+        if (status) status[i] = r;
+        if (r != KG_OK) {
+            if (first_err == KG_OK) first_err = r;
+            continue;
+        }
+        eq_groups(G, cols, inst[i], i, orb, n_orb);
+    }
+    if (n_inst == 1 && first_err != KG_OK) return first_err;
+    if (cols.empty()) return n_inst == 1 ? KG_OK : first_err;
+    cudaStream_t st = pick_stream(inst[0], o);
+    // every column keeps M; a sector smaller than M ends its space by a happy
+    // breakdown (the recursion is exact once it spans the sector)
+    const int Mb = o->M;
+    Krylov K;
+    int rc = krylov_alloc(K, cols, Mb, inst[0]->nsm, o->schedule != 1);
+    size_t n_ov = 0;
+    for (auto& g : G) {
+        const size_t na = g.idx.size();
+        n_ov += na * rows * na;
+        if (rc == KG_OK && cudaMalloc(&g.chi, sizeof(double2) * na * g.nb->d) != cudaSuccess) rc = KG_ENOMEM;
+    }
+    double2* ov = nullptr;
+    if (rc == KG_OK && cudaMalloc(&ov, sizeof(double2) * std::max<size_t>(1, n_ov)) != cudaSuccess) rc = KG_ENOMEM;
+    if (rc == KG_OK) rc = eq_run(G, inst, orb, K, ov, rows, dt, n_steps, o, tune, st);
+    std::vector<double2> hov(n_ov);
+    if (rc == KG_OK &&
+        (cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * n_ov, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        rc = cuda_fail(cudaGetLastError(), "overlap readback", __FILE__, __LINE__);
+    std::vector<ColScalars> hcs;
+    if (rc == KG_OK) {
+        hcs.resize(K.B);
+        if (cudaMemcpy(hcs.data(), K.cs, sizeof(ColScalars) * K.B, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = KG_ECUDA;
+    }
+    if (rc == KG_OK) {
+        for (auto& g : G) {
+            bool bad = false;
+            for (size_t a = 0; a < g.idx.size(); ++a) bad |= hcs[g.col0 + a].status == KG_ENUMERIC;
+            if (bad) {
+                if (status) status[g.inst] = KG_ENUMERIC;
+                if (n_inst == 1) {
+                    set_error("non-finite value during propagation");
+                    rc = KG_ENUMERIC;
+                }
+                continue;
+            }
+            eq_assemble(g, hov, rows, dt, inst[g.inst]->E0, n_orb, G_gtr + per_inst * g.inst,
+                        G_les + per_inst * g.inst);
+        }
+    }
+    for (auto& g : G) cudaFree(g.chi);
+    cudaFree(ov);
+    krylov_free(K);
+    return rc;
+}
+
+int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
+                      double* G_gtr, double* G_les) {
+    return green_eq_batch(&s, 1, orb, n_orb, dt, n_steps, o, G_gtr, G_les, nullptr, false);
+}
+
+int green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
+                              const kg_opts* o, double* G_gtr, double* G_les, int* status) {
+    if (!s || n_inst < 1) {
+        set_error("no instances");
+        return KG_EINVAL;
+    }
+    return green_eq_batch(s, n_inst, orb, n_orb, dt, n_steps, o, G_gtr, G_les, status, true);
 }
 
 // --------------------------------------------------- a7: Gram, step (iv)
@@ -362,16 +484,13 @@ static void block_release(KBlock& B) {
 static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
     if (B.ready) return KG_OK;
     const int na = (int)B.idx.size(), dn = (int)B.nb->d;
-    KG_TRY(krylov_alloc(B.K, na, std::min(X->o.M, dn), dn, X->fin->nsm));
+    std::vector<const kg_sector*> cols(na, B.nb);
+    KG_TRY(krylov_alloc(B.K, cols, std::min(X->o.M, dn), X->fin->nsm, X->o.schedule != 1));
+    for (auto& D : B.K.hdesc) D.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
+    KG_TRY(krylov_upload(B.K, st));
     KG_CUDA(cudaMalloc(&B.store, sizeof(double2) * (size_t)X->n_t * na * dn));
     KG_CUDA(cudaMalloc(&B.ovbuf, sizeof(double2) * (size_t)na * na));
-    StepPlan P;
-    P.sec = B.nb;
-    P.K = &B.K;
-    P.reorth = X->o.reorth;
-    P.int_hops = X->o.schedule != 1;
-    P.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
-    KG_TRY(B.R.init(P, st, X->o.use_graphs != 0));
+    KG_TRY(B.R.init(B.K, X->o.reorth, st, X->o.use_graphs != 0));
     B.ready = true;
     return KG_OK;
 }
@@ -382,8 +501,8 @@ static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
     for (int a = 0; a < na; ++a)
         KG_TRY(launch_cop(X->fin, B.nb, X->orb[2 * B.idx[a]], B.spin, B.dagger, phik, B.K.vec(a, 0), st));
     for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));
-    KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)k * na * dn, (size_t)dn * sizeof(double2), B.K.V,
-                              B.K.colV() * sizeof(double2), (size_t)dn * sizeof(double2), na,
+    KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)k * na * dn, (size_t)dn * sizeof(double2), B.K.vec(0, 0),
+                              (size_t)(B.K.M + 1) * dn * sizeof(double2), (size_t)dn * sizeof(double2), na,
                               cudaMemcpyDeviceToDevice, st));
     return KG_OK;
 }
@@ -452,24 +571,26 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
         return fail(KG_ENOMEM);
     }
     // step (ii): Phi(t_k) = e^{-iH t_k} |0>, stored on the grid
-    KG_CUDA(cudaMemcpyAsync(X->phi, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st));
+    if (cudaMemcpyAsync(X->phi, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return fail(KG_ECUDA);
     if (n_t > 1) {
         Krylov K;
         StepRunner R;
-        int rc = krylov_alloc(K, 1, std::min(o->M, (int)d), (int)d, fin->nsm);
-        StepPlan P;
-        P.sec = fin;
-        P.K = &K;
-        P.reorth = o->reorth;
-        P.int_hops = o->schedule != 1;
-        P.tau = dt / X->n_sub;
+        int rc = krylov_alloc(K, {fin}, std::min(o->M, (int)d), fin->nsm, o->schedule != 1);
+        if (rc == KG_OK) {
+            K.hdesc[0].tau = dt / X->n_sub;
+            rc = krylov_upload(K, st);
+        }
         if (rc == KG_OK)
-            rc = cudaMemcpyAsync(K.V, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-        if (rc == KG_OK) rc = R.init(P, st, o->use_graphs != 0);
+            rc = cudaMemcpyAsync(K.vec(0, 0), ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                     ? KG_OK
+                     : KG_ECUDA;
+        if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
         for (int k = 1; rc == KG_OK && k < n_t; ++k) {
             for (int n = 0; rc == KG_OK && n < X->n_sub; ++n) rc = R.run(st);
             if (rc == KG_OK)
-                rc = cudaMemcpyAsync(X->phi + k * d, K.V, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                rc = cudaMemcpyAsync(X->phi + k * d, K.vec(0, 0), sizeof(double2) * d, cudaMemcpyDeviceToDevice,
+                                     st) == cudaSuccess
                          ? KG_OK
                          : KG_ECUDA;
         }
@@ -517,9 +638,8 @@ int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk) {
         KG_TRY(block_prepare(X, B, st));
         KG_TRY(block_row(X, B, k, st));
         const int na = (int)B.idx.size(), dn = (int)B.nb->d;
-        KG_TRY(reset_slots(B.K, st));
         const double2* xs = B.store + (size_t)k * na * dn;
-        KG_TRY(launch_overlaps_cs(B.K, xs, dn, xs, na, dn, B.ovbuf, 1, st));
+        KG_TRY(launch_inner_lib(xs, na, xs, na, dn, B.ovbuf, na, st));
         std::vector<double2> h((size_t)na * na);
         KG_CUDA(cudaMemcpyAsync(h.data(), B.ovbuf, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
         KG_CUDA(cudaStreamSynchronize(st));

@@ -162,31 +162,32 @@ __global__ void __launch_bounds__(kThreads) k_hpsi(SecView S, const double2* __r
     }
 }
 
-// Lanczos step j for column b = blockIdx.y:
+// Lanczos step j for column b of a work-list launch:
 //   w = s_j H V_j - b_j s_{j-1} V_{j-1},   a_j = Re <s_j V_j, w>
 // (Eq. (recursion) with normalised v_k = s_k V_k).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(SecView S, double2* __restrict__ V, size_t colV,
-                                                           double2* __restrict__ W, ColScalars* cs, int j,
-                                                           double* part, unsigned* cnt, int pstride) {
+__global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                           int j, unsigned* cnt) {
     __shared__ double2 amp[kMaxL * kMaxL];
     __shared__ double utab[4 * 256];
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ double bs[2], red[2];
-    const int b = blockIdx.y;
-    ColScalars* C = cs + b;
+    __shared__ SecView S;
+    KG_ITEM();
     if (j >= C->m_eff) return;
+    if (threadIdx.x == 0) S = *D.sec;
+    __syncthreads();
     stage_tables(S, amp, utab);
     const double sj = C->scale[j];
     const double cprev = (j > 0) ? C->beta[j] * C->scale[j - 1] : 0.0;
     const int E = (MODE == 3) ? C->emax[j] : 0;
     const double unit = (MODE == 3) ? fix_unit(E, S.fix_pre) * S.h0 * sj : 0.0;
     const double hs = S.h0 * sj;
-    const double2* x = V + (size_t)b * colV + (size_t)j * S.d;
-    const double2* xp = V + (size_t)b * colV + (size_t)(j > 0 ? j - 1 : 0) * S.d;
-    double2* w = W + (size_t)b * S.d;
+    const double2* x = D.V + (size_t)j * D.d;
+    const double2* xp = D.V + (size_t)(j > 0 ? j - 1 : 0) * D.d;
+    double2* w = D.W;
     double acc[2] = {0.0, 0.0};
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.d; idx += gridDim.x * blockDim.x) {
+    KG_FOR(idx) {
         int i_dn, i_up;
         split_index(S, idx, i_dn, i_up);
         const double2 xv = x[idx];
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(SecView S, double2* _
     }
     acc[0] *= sj;
     block_sum<2>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red)) {
+    if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red)) {
         if (threadIdx.x == 0) {
             const double a = red[0];
             C->alpha[j] = a;
@@ -252,22 +253,41 @@ int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st)
     return KG_OK;
 }
 
-int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, bool int_hops, cudaStream_t st) {
-    const int mode = S.hopmode == 0 ? ((int_hops && S.fix_pre >= 0) ? 3 : 0) : S.hopmode;
-    const void* kern = mode == 3   ? (const void*)k_lanczos_hpsi<3>
-                       : mode == 0 ? (const void*)k_lanczos_hpsi<0>
-                       : mode == 1 ? (const void*)k_lanczos_hpsi<1>
-                                   : (const void*)k_lanczos_hpsi<2>;
-    dim3 grid(wave_blocks(K, kern), K.B);
-    const int pst = K.nblk * kPart;
-    ProfScope ps("lanczos_hpsi", st);
-    switch (mode) {
-        case 3: k_lanczos_hpsi<3><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
-        case 0: k_lanczos_hpsi<0><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
-        case 1: k_lanczos_hpsi<1><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
-        default: k_lanczos_hpsi<2><<<grid, kThreads, 0, st>>>(S, K.V, K.colV(), K.W, K.cs, j, K.part, K.cnt, pst); break;
+int prepare_hpsi_lists(Krylov& K) {
+    bool present[4] = {false, false, false, false};
+    for (auto& D : K.hdesc) present[D.mode] = true;
+    const void* kerns[4] = {(const void*)k_lanczos_hpsi<0>, (const void*)k_lanczos_hpsi<1>,
+                            (const void*)k_lanczos_hpsi<2>, (const void*)k_lanczos_hpsi<3>};
+    for (int mode = 0; mode < 4; ++mode) {
+        if (!present[mode]) continue;
+        const int4* items;
+        int n;
+        KG_TRY(work_list(K, kerns[mode], mode, &items, &n));
     }
-    KG_LAUNCHED();
+    return KG_OK;
+}
+
+int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st) {
+    bool present[4] = {false, false, false, false};
+    for (auto& D : K.hdesc) present[D.mode] = true;
+    ProfScope ps("lanczos_hpsi", st);
+    for (int mode = 0; mode < 4; ++mode) {
+        if (!present[mode]) continue;
+        const void* kern = mode == 3   ? (const void*)k_lanczos_hpsi<3>
+                           : mode == 0 ? (const void*)k_lanczos_hpsi<0>
+                           : mode == 1 ? (const void*)k_lanczos_hpsi<1>
+                                       : (const void*)k_lanczos_hpsi<2>;
+        const int4* items;
+        int n;
+        KG_TRY(work_list(K, kern, mode, &items, &n));
+        switch (mode) {
+            case 3: k_lanczos_hpsi<3><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+            case 0: k_lanczos_hpsi<0><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+            case 1: k_lanczos_hpsi<1><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+            default: k_lanczos_hpsi<2><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+        }
+        KG_LAUNCHED();
+    }
     return KG_OK;
 }
 

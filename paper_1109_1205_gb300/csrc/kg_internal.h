@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -127,34 +129,61 @@ struct ColScalars {
     int pad;
 };
 
-// B independent columns (vectors) of one sector, each with its own Lanczos
-// basis V[b][0..M] of dimension d.
-struct Krylov {
-    int B = 0, M = 0, d = 0;
-    int nsm = 148;
-    int nblk = 1;               // partial-sum rows per column (>= blocks per column of any launch)
-    double2* V = nullptr;       // [B][M+1][d]
-    double2* W = nullptr;       // [B][d]
-    ColScalars* cs = nullptr;   // [B]
-    double* part = nullptr;     // [B][nblk][kPart]
-    unsigned* cnt = nullptr;    // [B]
-    double* Q = nullptr;        // [B][M*M] eigenvectors of T
-    size_t colV() const { return (size_t)(M + 1) * (size_t)d; }
-    double2* vec(int b, int k) const { return V + (size_t)b * colV() + (size_t)k * d; }
+// One column of a Krylov batch.  Columns are independent vectors, each with
+// its own sector (dimension, tables), its own Lanczos basis and step tau;
+// the device copy is read by every kernel of a step.
+struct ColDesc {
+    const SecView* sec;     // this column's sector (device copy)
+    double2* V;             // [M+1][d] Lanczos vectors (unnormalised)
+    double2* W;             // [d] H v workspace
+    double* part;           // [nblk_max][kPart] partial sums of this column
+    double2* out;           // where the combination writes (V_0 by default)
+    const double2* ov;      // n_ov overlap vectors, stride ov_stride
+    double2* ov_out;        // overlap rows [ov_rows][n_ov]
+    long long ov_stride;
+    double tau;             // propagation step of this column
+    int d, n_ov, ov_rows, nblk_max;
+    int mode;               // hop sums: 0 FP64 uniform, 1 real, 2 complex, 3 exact integer
+    int pad;
 };
 
-int krylov_alloc(Krylov& K, int B, int M, int d, int nsm);
-// Blocks per column for a one-wave launch of `kern` over the B columns of K.
-int wave_blocks(const Krylov& K, const void* kern, size_t smem = 0);
+// B columns of (possibly) different sectors.  Every streaming kernel runs over
+// a work list of (column, block, blocks of that column) items sized from the
+// kernel's occupancy and each column's dimension, so that one launch of a
+// phase covers every column of the batch in about one wave.
+struct Krylov {
+    int B = 0, M = 0, nsm = 148;
+    long long total_d = 0;
+    double wave_scale = 1.0;        // work-list size relative to one wave (tuned)
+    std::vector<ColDesc> hdesc;     // host copy (device addresses)
+    std::vector<SecView> hsec;
+    ColDesc* desc = nullptr;        // [B]
+    SecView* secs = nullptr;        // [B]
+    ColScalars* cs = nullptr;       // [B]
+    unsigned* cnt = nullptr;        // [B]
+    double* Q = nullptr;            // [B][M*M] eigenvectors of T
+    double2* Vbuf = nullptr;
+    double2* Wbuf = nullptr;
+    double* partbuf = nullptr;
+    std::map<long long, std::pair<int4*, int>> lists;
+    double2* vec(int b, int k) const { return hdesc[b].V + (size_t)k * hdesc[b].d; }
+    int dim(int b) const { return hdesc[b].d; }
+};
+
+// One column per entry of `cols` (sectors may repeat).  int_hops selects the
+// exact integer hop sums for sectors with uniform hopping.
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, bool int_hops);
+int krylov_upload(Krylov& K, cudaStream_t st);  // after editing hdesc (tau, out, overlaps)
 void krylov_free(Krylov& K);
+int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n);
 
 // ----------------------------------------------------------- launchers
 // a2: y = H x (plain).
 int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st);
 // a2+a3: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
 // partial sums of a_j = <v_j, w> reduced on the device.
-int launch_lanczos_hpsi(const SecView& S, Krylov& K, int j, bool int_hops, cudaStream_t st);
-// start of a step: beta0 = ||V_0||, scale[0], m_eff = M, status reset.
+int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st);
+// start of a step: beta0 = ||V_0||, scale[0], largest exponent, m_eff = M.
 int launch_colnorm(Krylov& K, cudaStream_t st);
 // a3 reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or
 // h_k = <v_k, V_{j+1}> (second pass) for k in [k0, k0 + nk).
@@ -162,17 +191,14 @@ int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream
 // a3 update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
 // second pass), then b_{j+1} = ||V_{j+1}||, scale, breakdown test.
 int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st);
-// a4: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1;
-// mode 1: ground-state Ritz pair (lam0, c = q_0).
-int launch_tridiag(Krylov& K, int mode, double tau, cudaStream_t st);
-// a5 + a7: out_b = sum_k c_k V_k; ||out_b||; overlaps <ov_a, out_b>.
-int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov, int n_ov,
-                   size_t ov_stride, double2* ov_out, int ov_rows, bool renorm_v0,
-                   cudaStream_t st);
-// overlaps of arbitrary vectors: out[b][a] = <ov_a, x_b> (a7), one slot.
-int launch_overlaps(int B, int d, const double2* x, size_t x_stride, const double2* ov, int n_ov,
-                    size_t ov_stride, double2* out, double* part, unsigned* cnt, int nblk,
-                    cudaStream_t st);
+// a4: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1
+// with each column's tau; mode 1: ground-state Ritz pair (lam0, c = q_0).
+int launch_tridiag(Krylov& K, int mode, cudaStream_t st);
+// a5 + a7: out = sum_k c_k V_k per column; ||out||; overlaps <ov_a, out>.
+int launch_combine(Krylov& K, cudaStream_t st);
+// a7: G[b*g_stride + a] = <x_a | y_b> (kg_overlap.cu), library scratch.
+int launch_inner_lib(const double2* X, int n_x, const double2* Y, int n_y, int d, double2* G, int g_stride,
+                     cudaStream_t st);
 // a6: y = c / c^dag x between neighbouring sectors.
 int launch_cop(const kg_sector* src, const kg_sector* dst, int site, int spin, int dagger,
                const double2* x, double2* y, cudaStream_t st);
@@ -187,26 +213,37 @@ void sector_free(kg_sector* s);
 int neighbour(kg_sector* s, int spin, int dagger, kg_sector** out);
 cudaStream_t pick_stream(const kg_sector* s, const kg_opts* o);
 
-// One propagation step exp(-i H tau) of every column of K, starting from
-// V[b][0] and leaving the result in V[b][0] (a2-a5).  Optional fused
-// overlaps of the result with n_ov vectors.
-struct StepPlan {
-    const kg_sector* sec = nullptr;
+// One propagation step exp(-i H tau_b) of every column b of K, starting from
+// V[b][0] and leaving the result at desc[b].out (V[b][0] unless changed),
+// with the overlaps configured in the column descriptors (a2-a5, a7).
+int enqueue_step(Krylov& K, int reorth, cudaStream_t st);
+// Builds every work list a step uses (device allocations) so that the step
+// can then be captured into a graph, where allocation is not allowed.
+int prepare_step(Krylov& K, int reorth);
+int prepare_hpsi_lists(Krylov& K);
+// Sets the overlap row counter of every column.
+int launch_set_slots(Krylov& K, int value, cudaStream_t st);
+
+// Replays the launch sequence of one propagation step, as a CUDA graph when
+// allowed (the sequence is fixed: iteration counts and early exits after a
+// breakdown are decided on the device).
+struct StepRunner {
     Krylov* K = nullptr;
     int reorth = 1;
-    int int_hops = 1;           // exact integer hop sums when the hopping is uniform
-    double tau = 0.0;
-    const double2* ov = nullptr;
-    int n_ov = 0;
-    size_t ov_stride = 0;
-    double2* ov_out = nullptr;
-    int ov_rows = 0;
+    cudaGraphExec_t exec = nullptr;
+    size_t nodes = 0;
+    bool graph = false;
+    int init(Krylov& k, int reorth_mode, cudaStream_t st, bool use_graph);
+    int run(cudaStream_t st);
+    void release();
 };
-int enqueue_step(const StepPlan& P, cudaStream_t st);
 
 int ground_state(kg_sector* s, const kg_opts* o);
 int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
                       double* G_gtr, double* G_les);
+int green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
+                              const kg_opts* o, double* G_gtr, double* G_les, int* status);
+int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<double>>& G, cudaStream_t st);
 int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                    const kg_opts* o, kg_keldysh** out);
 void keldysh_free(kg_keldysh* X);
@@ -293,6 +330,15 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], int nv, double*
     __syncthreads();
 }
 
+// A block of a work-list launch: its column b, its index blk among the nblk
+// blocks of that column, the column descriptor D and scalars C.
+#define KG_ITEM()                                   \
+    const int4 it_ = items[blockIdx.x];             \
+    const int b = it_.x, blk = it_.y, nblk = it_.z; \
+    const ColDesc D = desc[b];                      \
+    ColScalars* C = cs + b
+#define KG_FOR(i) for (int i = blk * blockDim.x + threadIdx.x; i < D.d; i += nblk * blockDim.x)
+
 // Block maximum of an int (valid in thread 0 only).
 __device__ __forceinline__ int block_max_int(int v, int* sm) {
     v = __reduce_max_sync(0xffffffffu, v);
@@ -310,18 +356,17 @@ __device__ __forceinline__ int exp_field(double x) {
     return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
 }
 
-// Deterministic grid reduction over the gridDim.x blocks of one column.
+// Deterministic reduction over the nblk blocks of one column (block `row`).
 // Each block stores its nv + nmax totals (bsum, in shared memory) into its
 // row of part; the last block to arrive (atomic ticket) combines the rows in
 // a fixed order into red (shared): values [0, nv) are summed, values
 // [nv, nv + nmax) max-reduced.  It resets the ticket and returns true; other
 // blocks return false.
-__device__ __forceinline__ bool grid_finish(const double* bsum, int nv, double* part, unsigned* cnt,
-                                            int /*unused*/, double* red, int nmax = 0) {
+__device__ __forceinline__ bool grid_finish(const double* bsum, int nv, double* part, unsigned* cnt, int row,
+                                            int nblk, double* red, int nmax = 0) {
     __shared__ unsigned ticket;
-    const int nblk = gridDim.x;
     const int nt = nv + nmax;
-    for (int k = threadIdx.x; k < nt; k += blockDim.x) part[(size_t)blockIdx.x * kPart + k] = bsum[k];
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) part[(size_t)row * kPart + k] = bsum[k];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(cnt, 1u);

@@ -3,10 +3,13 @@
 // and the basis combination (Section 2, Eqs. (recursion), (tmatrix),
 // (tdiag), (eigen); Section 3, Eqs. (newstate) and (udelta)).
 //
-// Every kernel works on B independent columns (blockIdx.y = column) of one
-// sector.  Lanczos vectors are stored unnormalised, V_k, with v_k = s_k V_k
-// and s_k = 1/||V_k|| kept on the device, so normalisation never costs a
-// separate pass.  Scalars (a_k, b_k, Gram-Schmidt coefficients, combination
+// Every kernel works on a batch of B independent columns, possibly of
+// different sectors and dimensions (many instances, or many columns of one
+// Green's-function calculation).  A launch walks a work list of (column,
+// block, blocks-of-that-column) items, so one launch per phase serves the
+// whole batch.  Lanczos vectors are stored unnormalised, V_k, with v_k = s_k
+// V_k and s_k = 1/||V_k|| kept on the device, so normalisation never costs a
+// separate pass.  Scalars (a_k, b_k, Gram-Schmidt and combination
 // coefficients) never leave the device: a whole propagation step is a fixed
 // launch sequence that a CUDA graph can replay.
 #include <algorithm>
@@ -19,68 +22,136 @@
 
 namespace kg {
 
-int krylov_alloc(Krylov& K, int B, int M, int d, int nsm) {
+// ------------------------------------------------------------ workspace
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, bool int_hops) {
     K = Krylov();
-    K.B = B;
+    K.B = (int)cols.size();
     K.M = M;
-    K.d = d;
     K.nsm = nsm;
-    // partial-sum rows: enough for a one-wave launch of any kernel (<= 8
-    // resident 256-thread blocks per SM) spread over the B columns
-    K.nblk = std::max(1, std::min((d + kThreads - 1) / kThreads, (nsm * 8 + B - 1) / B));
-    const size_t nv = (size_t)B * (M + 1) * (size_t)d;
-    KG_CUDA(cudaMalloc(&K.V, sizeof(double2) * nv));
-    KG_CUDA(cudaMalloc(&K.W, sizeof(double2) * (size_t)B * d));
-    KG_CUDA(cudaMalloc(&K.cs, sizeof(ColScalars) * B));
-    KG_CUDA(cudaMalloc(&K.part, sizeof(double) * (size_t)B * K.nblk * kPart));
-    KG_CUDA(cudaMalloc(&K.cnt, sizeof(unsigned) * B));
-    KG_CUDA(cudaMalloc(&K.Q, sizeof(double) * (size_t)B * M * M));
-    KG_CUDA(cudaMemset(K.cs, 0, sizeof(ColScalars) * B));
-    KG_CUDA(cudaMemset(K.cnt, 0, sizeof(unsigned) * B));
+    if (K.B < 1) {
+        set_error("empty Krylov batch");
+        return KG_EINVAL;
+    }
+    size_t nv = 0, nw = 0, np = 0;
+    for (auto* s : cols) K.total_d += s->d;
+    K.hdesc.resize(K.B);
+    K.hsec.resize(K.B);
+    for (int b = 0; b < K.B; ++b) {
+        const kg_sector* s = cols[b];
+        ColDesc& D = K.hdesc[b];
+        std::memset(&D, 0, sizeof D);
+        D.d = (int)s->d;
+        // partial-sum rows: enough for a one-wave list (<= 8 blocks per SM)
+        // of any kernel at up to twice the wave, shared in proportion to d
+        const long long want = (long long)std::ceil(16.0 * nsm * (double)s->d / (double)K.total_d) + 2;
+        D.nblk_max = (int)std::max(1LL, std::min(want, (long long)(s->d + kThreads - 1) / kThreads));
+        K.hsec[b] = s->view();
+        const SecView& S = K.hsec[b];
+        D.mode = S.hopmode == 0 ? ((int_hops && S.fix_pre >= 0) ? 3 : 0) : S.hopmode;
+        nv += (size_t)(M + 1) * D.d;
+        nw += (size_t)D.d;
+        np += (size_t)D.nblk_max * kPart;
+    }
+    KG_CUDA(cudaMalloc(&K.Vbuf, sizeof(double2) * nv));
+    KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * nw));
+    KG_CUDA(cudaMalloc(&K.partbuf, sizeof(double) * np));
+    KG_CUDA(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B));
+    KG_CUDA(cudaMalloc(&K.secs, sizeof(SecView) * K.B));
+    KG_CUDA(cudaMalloc(&K.cs, sizeof(ColScalars) * K.B));
+    KG_CUDA(cudaMalloc(&K.cnt, sizeof(unsigned) * K.B));
+    KG_CUDA(cudaMalloc(&K.Q, sizeof(double) * (size_t)K.B * M * M));
+    KG_CUDA(cudaMemset(K.cs, 0, sizeof(ColScalars) * K.B));
+    KG_CUDA(cudaMemset(K.cnt, 0, sizeof(unsigned) * K.B));
+    size_t ov = 0, ow = 0, op = 0;
+    for (int b = 0; b < K.B; ++b) {
+        ColDesc& D = K.hdesc[b];
+        D.sec = K.secs + b;
+        D.V = K.Vbuf + ov;
+        D.W = K.Wbuf + ow;
+        D.part = K.partbuf + op;
+        D.out = D.V;
+        ov += (size_t)(M + 1) * D.d;
+        ow += (size_t)D.d;
+        op += (size_t)D.nblk_max * kPart;
+    }
+    KG_CUDA(cudaMemcpy(K.secs, K.hsec.data(), sizeof(SecView) * K.B, cudaMemcpyHostToDevice));
+    KG_CUDA(cudaMemcpy(K.desc, K.hdesc.data(), sizeof(ColDesc) * K.B, cudaMemcpyHostToDevice));
     return KG_OK;
 }
 
-int wave_blocks(const Krylov& K, const void* kern, size_t smem) {
-    static std::mutex mu;
-    static std::map<const void*, int> occ;
-    int bps = 0;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = occ.find(kern);
-        if (it == occ.end()) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kThreads, smem) != cudaSuccess || bps < 1)
-                bps = 1;
-            occ[kern] = bps;
-        } else {
-            bps = it->second;
-        }
-    }
-    const int per = std::max(1, (K.nsm * bps) / K.B);
-    return std::max(1, std::min(per, K.nblk));
+int krylov_upload(Krylov& K, cudaStream_t st) {
+    KG_CUDA(cudaMemcpyAsync(K.desc, K.hdesc.data(), sizeof(ColDesc) * K.B, cudaMemcpyHostToDevice, st));
+    return KG_OK;
 }
 
 void krylov_free(Krylov& K) {
-    cudaFree(K.V);
-    cudaFree(K.W);
+    for (auto& kv : K.lists) cudaFree(kv.second.first);
+    cudaFree(K.Vbuf);
+    cudaFree(K.Wbuf);
+    cudaFree(K.partbuf);
+    cudaFree(K.desc);
+    cudaFree(K.secs);
     cudaFree(K.cs);
-    cudaFree(K.part);
     cudaFree(K.cnt);
     cudaFree(K.Q);
     K = Krylov();
 }
 
+static int occupancy(const void* kern) {
+    static std::mutex mu;
+    static std::map<const void*, int> occ;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find(kern);
+    if (it != occ.end()) return it->second;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kThreads, 0) != cudaSuccess || bps < 1) bps = 1;
+    occ[kern] = bps;
+    return bps;
+}
+
+// Work list of a kernel over the columns whose mode is `mode` (-1: all):
+// column b gets blocks in proportion to its dimension, one wave in total.
+int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n) {
+    const int bps = occupancy(kern);
+    const long long key = ((long long)bps << 8) + (mode + 1) + ((long long)std::lround(K.wave_scale * 64.0) << 20);
+    auto it = K.lists.find(key);
+    if (it == K.lists.end()) {
+        long long dsel = 0;
+        for (auto& D : K.hdesc)
+            if (mode < 0 || D.mode == mode) dsel += D.d;
+        const double total = std::max(1.0, K.wave_scale * K.nsm * bps);
+        std::vector<int4> v;
+        for (int b = 0; b < K.B; ++b) {
+            const ColDesc& D = K.hdesc[b];
+            if (mode >= 0 && D.mode != mode) continue;
+            int nb = (int)std::lround(total * (double)D.d / (double)std::max(1LL, dsel));
+            nb = std::max(1, std::min(nb, std::min(D.nblk_max, (D.d + kThreads - 1) / kThreads)));
+            for (int k = 0; k < nb; ++k) v.push_back(make_int4(b, k, nb, 0));
+        }
+        int4* d = nullptr;
+        if (!v.empty()) {
+            KG_CUDA(cudaMalloc(&d, sizeof(int4) * v.size()));
+            KG_CUDA(cudaMemcpy(d, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice));
+        }
+        it = K.lists.emplace(key, std::make_pair(d, (int)v.size())).first;
+    }
+    *items = it->second.first;
+    *n = it->second.second;
+    return KG_OK;
+}
+
 // ------------------------------------------------- start-of-step norm
 // beta0 = ||V_0||, s_0, the largest exponent of V_0, m_eff = M.
-__global__ void __launch_bounds__(kThreads) k_colnorm(double2* V, size_t colV, int d, ColScalars* cs, int M,
-                                                      double* part, unsigned* cnt, int pstride) {
+__global__ void __launch_bounds__(kThreads) k_colnorm(const ColDesc* desc, const int4* items, ColScalars* cs, int M,
+                                                      unsigned* cnt) {
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
-    const int b = blockIdx.y;
-    const double2* x = V + (size_t)b * colV;
+    KG_ITEM();
+    const double2* x = D.V;
     double acc[1] = {0.0};
     int em = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+    KG_FOR(i) {
         const double2 v = x[i];
         acc[0] = fma(v.x, v.x, fma(v.y, v.y, acc[0]));
         em = max(em, max(exp_field(v.x), exp_field(v.y)));
@@ -89,8 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(double2* V, size_t colV, i
     block_sum<1>(acc, 1, sm, bs);
     if (threadIdx.x == 0) bs[1] = (double)em;
     __syncthreads();
-    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red, 1) && threadIdx.x == 0) {
-        ColScalars* C = cs + b;
+    if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red, 1) && threadIdx.x == 0) {
         const double n = sqrt(red[0]);
         C->beta0 = n;
         C->beta[0] = 0.0;
@@ -104,8 +174,10 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(double2* V, size_t colV, i
 
 int launch_colnorm(Krylov& K, cudaStream_t st) {
     ProfScope ps("colnorm", st);
-    k_colnorm<<<dim3(wave_blocks(K, (const void*)k_colnorm), K.B), kThreads, 0, st>>>(
-        K.V, K.colV(), K.d, K.cs, K.M, K.part, K.cnt, K.nblk * kPart);
+    const int4* items;
+    int n;
+    KG_TRY(work_list(K, (const void*)k_colnorm, -1, &items, &n));
+    k_colnorm<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, K.M, K.cnt);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -116,22 +188,21 @@ int launch_colnorm(Krylov& K, cudaStream_t st) {
 // NK (compile time) bounds nk so that the accumulators stay in registers
 // without holding 64 of them when only a few vectors are needed.
 template <int NK>
-__global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t colV, const double2* W, int d,
-                                                          ColScalars* cs, int j, int k0, int nk, int second,
-                                                          double* part, unsigned* cnt, int pstride) {
+__global__ void __launch_bounds__(kThreads) k_reorth_dots(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                          int j, int k0, int nk, int second, unsigned* cnt) {
     __shared__ double sm[(kThreads / 32) * 2 * NK];
     __shared__ double bs[2 * NK], red[2 * NK];
-    const int b = blockIdx.y;
-    ColScalars* C = cs + b;
+    KG_ITEM();
     if (j >= C->m_eff) return;
-    const double2* Vb = V + (size_t)b * colV;
-    const double2* w = second ? Vb + (size_t)(j + 1) * d : W + (size_t)b * d;
+    const int d = D.d;
+    const double2* Vb = D.V;
+    const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
     const double2* vj = Vb + (size_t)j * d;
     const double aj = second ? 0.0 : C->alpha[j] * C->scale[j];
     double acc[2 * NK];
 #pragma unroll
     for (int k = 0; k < 2 * NK; ++k) acc[k] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+    KG_FOR(i) {
         double2 u = w[i];
         if (!second) {
             const double2 p = vj[i];
@@ -148,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t col
         }
     }
     block_sum<2 * NK>(acc, 2 * nk, sm, bs);
-    if (grid_finish(bs, 2 * nk, part + (size_t)b * pstride, cnt + b, 0, red)) {
+    if (grid_finish(bs, 2 * nk, D.part, cnt + b, blk, nblk, red)) {
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const double s = C->scale[k0 + k];
             C->h[k0 + k] = make_double2(s * red[2 * k], s * red[2 * k + 1]);
@@ -159,9 +230,13 @@ __global__ void __launch_bounds__(kThreads) k_reorth_dots(double2* V, size_t col
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
     ProfScope ps("reorth_dots", st);
     const int sec = second ? 1 : 0;
-    const int pst = K.nblk * kPart;
-#define KG_DOTS(NK) k_reorth_dots<NK><<<dim3(wave_blocks(K, (const void*)k_reorth_dots<NK>), K.B), kThreads, 0, st>>>( \
-        K.V, K.colV(), K.W, K.d, K.cs, j, k0, nk, sec, K.part, K.cnt, pst)
+    const int4* items;
+    int n;
+#define KG_DOTS(NK)                                                                         \
+    do {                                                                                    \
+        KG_TRY(work_list(K, (const void*)k_reorth_dots<NK>, -1, &items, &n));               \
+        k_reorth_dots<NK><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, k0, nk, sec, K.cnt); \
+    } while (0)
     if (nk <= 4) KG_DOTS(4);
     else if (nk <= 8) KG_DOTS(8);
     else if (nk <= 16) KG_DOTS(16);
@@ -175,9 +250,9 @@ int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream
 // ------------------------------------------------------ a3: the update
 // First pass:  V_{j+1} = W - a_j v_j - [reorth] sum_{k<=j} h_k v_k
 // Second pass: V_{j+1} -= sum_{k<=j} h_k v_k
-// then b_{j+1} = ||V_{j+1}||, s_{j+1} = 1/b_{j+1}, a_j += Re h_j, and the
-// breakdown test (the Krylov space is invariant when b_{j+1} is at rounding
-// level relative to |a_j| + b_j).
+// then b_{j+1} = ||V_{j+1}||, s_{j+1} = 1/b_{j+1}, a_j += Re h_j, the
+// largest exponent of V_{j+1}, and the breakdown test (the Krylov space is
+// invariant when b_{j+1} is at rounding level relative to |a_j| + b_j).
 //
 // After the three-term subtraction the Gram-Schmidt coefficients are at
 // rounding level (|h_k| ~ 1e-14 for unit vectors).  A term whose coefficient
@@ -187,19 +262,18 @@ int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream
 // than the FP64 pipe on this GPU.  Larger coefficients use FP64.
 constexpr double kSmallCoef = 1e-10;
 
-__global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, const double2* W, int d,
-                                                     ColScalars* cs, int j, int reorth, int second,
-                                                     double* part, unsigned* cnt, int pstride) {
+__global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const int4* items, ColScalars* cs, int j,
+                                                     int reorth, int second, unsigned* cnt) {
     __shared__ double2 coef[kMaxMgs + 1];
     __shared__ float2 coef32[kMaxMgs + 1];
     __shared__ int small[kMaxMgs + 1];
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
-    const int b = blockIdx.y;
-    ColScalars* C = cs + b;
+    KG_ITEM();
     if (j >= C->m_eff) return;
-    double2* Vb = V + (size_t)b * colV;
+    const int d = D.d;
+    double2* Vb = D.V;
     const int nk = reorth ? j + 1 : 0;
     for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         const double s = C->scale[k];
@@ -207,17 +281,16 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
         const double2 c = make_double2(s * h.x, s * h.y);
         coef[k] = c;
         coef32[k] = make_float2((float)c.x, (float)c.y);
-        // |c| relative to the unit vector v_k = s_k V_k
-        small[k] = (fabs(h.x) + fabs(h.y)) < kSmallCoef;
+        small[k] = (fabs(h.x) + fabs(h.y)) < kSmallCoef;  // |h_k| for the unit vector v_k
     }
     __syncthreads();
     const double aj = C->alpha[j] * C->scale[j];
-    const double2* w = second ? Vb + (size_t)(j + 1) * d : W + (size_t)b * d;
+    const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
     const double2* vj = Vb + (size_t)j * d;
     double2* out = Vb + (size_t)(j + 1) * d;
     double acc[1] = {0.0};
     int em = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+    KG_FOR(i) {
         double2 u = w[i];
         if (!second) {
             const double2 p = vj[i];
@@ -248,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
     block_sum<1>(acc, 1, sm, bs);
     if (threadIdx.x == 0) bs[1] = (double)em;
     __syncthreads();
-    if (grid_finish(bs, 1, part + (size_t)b * pstride, cnt + b, 0, red, 1) && threadIdx.x == 0) {
+    if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red, 1) && threadIdx.x == 0) {
         C->emax[j + 1] = (int)red[1];
         const double n = sqrt(red[0]);
         double a = C->alpha[j];
@@ -268,8 +341,10 @@ __global__ void __launch_bounds__(kThreads) k_update(double2* V, size_t colV, co
 
 int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
     ProfScope ps("update", st);
-    k_update<<<dim3(wave_blocks(K, (const void*)k_update), K.B), kThreads, 0, st>>>(
-        K.V, K.colV(), K.W, K.d, K.cs, j, reorth ? 1 : 0, second ? 1 : 0, K.part, K.cnt, K.nblk * kPart);
+    const int4* items;
+    int n;
+    KG_TRY(work_list(K, (const void*)k_update, -1, &items, &n));
+    k_update<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, reorth ? 1 : 0, second ? 1 : 0, K.cnt);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -279,7 +354,7 @@ int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
 // unreduced blocks of T (Golub and Van Loan, Section 8.3): lane 0 chases the
 // bulge and records the Givens rotations of one sweep in shared memory, then
 // all lanes apply them to their rows of Q (Q <- Q R_k).  On exit T = Q D Q^T.
-//   mode 0 (propagation, Eq. (udelta)):
+//   mode 0 (propagation, Eq. (udelta)), with the column's tau:
 //       c_k = beta0 * sum_m Q[k][m] e^{-i lambda_m tau} Q[0][m]
 //   mode 1 (ground state, Eq. (eigen)): c_k = Q[k][m0] for the lowest m0,
 //       lam0, lam1 = two lowest Ritz values, resest = |b_m Q[m-1][m0]|.
@@ -287,8 +362,8 @@ int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
 // unnormalised).
 constexpr int kTriWarps = 4;
 
-__global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(ColScalars* cs, int B, int Mcap, double* Qall, int mode,
-                                                           double tau) {
+__global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc, ColScalars* cs, int B, int Mcap,
+                                                           double* Qall, int mode) {
     __shared__ double sd[kTriWarps][kMaxMgs], se[kTriWarps][kMaxMgs];
     __shared__ double rc[kTriWarps][kMaxMgs], rs[kTriWarps][kMaxMgs];
     __shared__ int ctl[kTriWarps][4];
@@ -296,6 +371,7 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(ColScalars* cs, int 
     const int b = blockIdx.x * kTriWarps + warp;
     if (b >= B) return;
     ColScalars* C = cs + b;
+    const double tau = desc[b].tau;
     const int m = C->m_eff;
     double* Q = Qall + (size_t)b * Mcap * Mcap;
     double* d = sd[warp];
@@ -415,38 +491,37 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(ColScalars* cs, int 
     }
 }
 
-int launch_tridiag(Krylov& K, int mode, double tau, cudaStream_t st) {
+int launch_tridiag(Krylov& K, int mode, cudaStream_t st) {
     const int nb = (K.B + kTriWarps - 1) / kTriWarps;
     ProfScope ps("tridiag", st);
-    k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.cs, K.B, K.M, K.Q, mode, tau);
+    k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, mode);
     KG_LAUNCHED();
     return KG_OK;
 }
 
 // ----------------------------------- a5 + a7: combination and overlaps
-// out_b = sum_{k<m} c_k V_k  (Eq. (udelta) in the form V x small vector),
-// then ||out_b|| and <ov_a, out_b> for the n_ov overlap vectors, written to
-// row cs[b].ov_slot of ov_out (the slot advances by one).  NOV bounds n_ov at
-// compile time so that the accumulators stay in registers.
+// out = sum_{k<m} c_k V_k  (Eq. (udelta) in the form V x small vector), then
+// ||out|| and <ov_a, out> for the column's n_ov overlap vectors, written to
+// row cs[b].ov_slot of its overlap table (the slot advances by one).  NOV
+// bounds n_ov at compile time so that the accumulators stay in registers.
 template <int NOV>
-__global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t colV, int d, ColScalars* cs,
-                                                      double2* out, size_t out_stride, const double2* ov,
-                                                      int n_ov, size_t ov_stride, double2* ov_out, int ov_rows,
-                                                      double* part, unsigned* cnt, int pstride) {
+__global__ void __launch_bounds__(kThreads) k_combine(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                      unsigned* cnt) {
     __shared__ double2 coef[kMaxMgs];
     __shared__ double sm[(kThreads / 32) * (2 * NOV + 2)];
     __shared__ double bs[2 * NOV + 2], red[2 * NOV + 2];
-    const int b = blockIdx.y;
-    ColScalars* C = cs + b;
+    KG_ITEM();
     const int m = C->m_eff;
     for (int k = threadIdx.x; k < m; k += blockDim.x) coef[k] = C->c[k];
     __syncthreads();
-    const double2* Vb = V + (size_t)b * colV;
-    double2* o = out + (size_t)b * out_stride;
+    const int d = D.d;
+    const int n_ov = D.n_ov;
+    const double2* Vb = D.V;
+    double2* o = D.out;
     double acc[2 * NOV + 2];
 #pragma unroll
     for (int k = 0; k < 2 * NOV + 2; ++k) acc[k] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+    KG_FOR(i) {
         double2 u = make_double2(0.0, 0.0);
         for (int k = 0; k < m; ++k) {
             const double2 v = Vb[(size_t)k * d + i];
@@ -459,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
 #pragma unroll
         for (int a = 0; a < NOV; ++a) {
             if (a < n_ov) {
-                const double2 v = ov[(size_t)a * ov_stride + i];
+                const double2 v = D.ov[(size_t)a * D.ov_stride + i];
                 acc[2 + 2 * a] = fma(v.x, u.x, fma(v.y, u.y, acc[2 + 2 * a]));
                 acc[3 + 2 * a] = fma(v.x, u.y, fma(-v.y, u.x, acc[3 + 2 * a]));
             }
@@ -467,10 +542,10 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
     }
     const int nv = 2 + 2 * n_ov;
     block_sum<2 * NOV + 2>(acc, nv, sm, bs);
-    if (grid_finish(bs, nv, part + (size_t)b * pstride, cnt + b, 0, red)) {
+    if (grid_finish(bs, nv, D.part, cnt + b, blk, nblk, red)) {
         const int slot = C->ov_slot;
         for (int a = threadIdx.x; a < n_ov; a += blockDim.x)
-            if (slot < ov_rows) ov_out[((size_t)b * ov_rows + slot) * n_ov + a] = make_double2(red[2 + 2 * a], red[3 + 2 * a]);
+            if (slot < D.ov_rows) D.ov_out[(size_t)slot * n_ov + a] = make_double2(red[2 + 2 * a], red[3 + 2 * a]);
         __syncthreads();
         if (threadIdx.x == 0) {
             C->ovnorm = sqrt(red[0]);
@@ -479,16 +554,21 @@ __global__ void __launch_bounds__(kThreads) k_combine(const double2* V, size_t c
     }
 }
 
-int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov, int n_ov, size_t ov_stride,
-                   double2* ov_out, int ov_rows, bool, cudaStream_t st) {
+int launch_combine(Krylov& K, cudaStream_t st) {
+    int n_ov = 0;
+    for (auto& D : K.hdesc) n_ov = std::max(n_ov, D.n_ov);
     if (n_ov > kMaxOv) {
         set_error("at most %d overlap vectors per combination pass", kMaxOv);
         return KG_EINVAL;
     }
     ProfScope ps("combine", st);
-    const int pst = K.nblk * kPart;
-#define KG_COMB(NOV) k_combine<NOV><<<dim3(wave_blocks(K, (const void*)k_combine<NOV>), K.B), kThreads, 0, st>>>( \
-        K.V, K.colV(), K.d, K.cs, out, out_stride, ov, n_ov, ov_stride, ov_out, ov_rows, K.part, K.cnt, pst)
+    const int4* items;
+    int n;
+#define KG_COMB(NOV)                                                              \
+    do {                                                                          \
+        KG_TRY(work_list(K, (const void*)k_combine<NOV>, -1, &items, &n));        \
+        k_combine<NOV><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, K.cnt);       \
+    } while (0)
     if (n_ov == 0) KG_COMB(0);
     else if (n_ov <= 4) KG_COMB(4);
     else if (n_ov <= 12) KG_COMB(12);
@@ -498,57 +578,10 @@ int launch_combine(Krylov& K, double2* out, size_t out_stride, const double2* ov
     return KG_OK;
 }
 
-// Overlaps <ov_a, x_b> of arbitrary vectors into row cs[b].ov_slot (a7).
-__global__ void __launch_bounds__(kThreads) k_overlaps(const double2* x, size_t x_stride, int d, ColScalars* cs,
-                                                       const double2* ov, int n_ov, size_t ov_stride,
-                                                       double2* ov_out, int ov_rows, double* part, unsigned* cnt,
-                                                       int pstride) {
-    __shared__ double sm[(kThreads / 32) * 2 * kMaxOv];
-    __shared__ double bs[2 * kMaxOv], red[2 * kMaxOv];
-    const int b = blockIdx.y;
-    const double2* xb = x + (size_t)b * x_stride;
-    double acc[2 * kMaxOv];
-#pragma unroll
-    for (int k = 0; k < 2 * kMaxOv; ++k) acc[k] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
-        const double2 u = xb[i];
-#pragma unroll
-        for (int a = 0; a < kMaxOv; ++a) {
-            if (a < n_ov) {
-                const double2 v = ov[(size_t)a * ov_stride + i];
-                acc[2 * a] = fma(v.x, u.x, fma(v.y, u.y, acc[2 * a]));
-                acc[2 * a + 1] = fma(v.x, u.y, fma(-v.y, u.x, acc[2 * a + 1]));
-            }
-        }
-    }
-    block_sum<2 * kMaxOv>(acc, 2 * n_ov, sm, bs);
-    if (grid_finish(bs, 2 * n_ov, part + (size_t)b * pstride, cnt + b, 0, red)) {
-        ColScalars* C = cs + b;
-        const int slot = C->ov_slot;
-        for (int a = threadIdx.x; a < n_ov; a += blockDim.x)
-            if (slot < ov_rows) ov_out[((size_t)b * ov_rows + slot) * n_ov + a] = make_double2(red[2 * a], red[2 * a + 1]);
-        __syncthreads();
-        if (threadIdx.x == 0) C->ov_slot = slot + 1;
-    }
-}
-
-int launch_overlaps_cs(Krylov& K, const double2* x, size_t x_stride, const double2* ov, int n_ov, size_t ov_stride,
-                       double2* ov_out, int ov_rows, cudaStream_t st) {
-    if (n_ov > kMaxOv || n_ov < 1) {
-        set_error("1..%d overlap vectors per pass", kMaxOv);
-        return KG_EINVAL;
-    }
-    ProfScope ps("overlaps", st);
-    k_overlaps<<<dim3(wave_blocks(K, (const void*)k_overlaps), K.B), kThreads, 0, st>>>(
-        x, x_stride, K.d, K.cs, ov, n_ov, ov_stride, ov_out, ov_rows, K.part, K.cnt, K.nblk * kPart);
-    KG_LAUNCHED();
-    return KG_OK;
-}
-
 // -------------------------------------------- ground-state residual
 // rq = <x, y> (x normalised), then rnorm = ||y - rq x||.
 __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2* y, int d, ColScalars* cs,
-                                                 int phase, double* part, unsigned* cnt, int nblk) {
+                                                 int phase, double* part, unsigned* cnt) {
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ double bs[2], red[2];
     const double rq = phase ? cs->rq : 0.0;
@@ -563,7 +596,7 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
         }
     }
     block_sum<1>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, part, cnt, 0, red) && threadIdx.x == 0) {
+    if (grid_finish(bs, 1, part, cnt, blockIdx.x, gridDim.x, red) && threadIdx.x == 0) {
         if (phase == 0)
             cs->rq = red[0];
         else
@@ -572,24 +605,50 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
 }
 
 // -------------------------------------------------- step sequencing
-int enqueue_step(const StepPlan& P, cudaStream_t st) {
-    Krylov& K = *P.K;
-    const SecView S = P.sec->view();
+__global__ void k_set_slots(ColScalars* cs, int B, int value) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) cs[b].ov_slot = value;
+}
+
+int launch_set_slots(Krylov& K, int value, cudaStream_t st) {
+    k_set_slots<<<(K.B + 127) / 128, 128, 0, st>>>(K.cs, K.B, value);
+    KG_LAUNCHED();
+    return KG_OK;
+}
+
+int prepare_step(Krylov& K, int reorth) {
+    const int4* items;
+    int n;
+    KG_TRY(prepare_hpsi_lists(K));
+    KG_TRY(work_list(K, (const void*)k_colnorm, -1, &items, &n));
+    KG_TRY(work_list(K, (const void*)k_update, -1, &items, &n));
+    if (reorth >= 1) {
+        const void* dots[5] = {(const void*)k_reorth_dots<4>, (const void*)k_reorth_dots<8>,
+                               (const void*)k_reorth_dots<16>, (const void*)k_reorth_dots<24>,
+                               (const void*)k_reorth_dots<32>};
+        for (auto* k : dots) KG_TRY(work_list(K, k, -1, &items, &n));
+    }
+    const void* comb[4] = {(const void*)k_combine<0>, (const void*)k_combine<4>, (const void*)k_combine<12>,
+                           (const void*)k_combine<32>};
+    for (auto* k : comb) KG_TRY(work_list(K, k, -1, &items, &n));
+    return KG_OK;
+}
+
+int enqueue_step(Krylov& K, int reorth, cudaStream_t st) {
     KG_TRY(launch_colnorm(K, st));
     for (int j = 0; j < K.M; ++j) {
-        KG_TRY(launch_lanczos_hpsi(S, K, j, P.int_hops != 0, st));
-        if (P.reorth >= 1)
+        KG_TRY(launch_lanczos_hpsi(K, j, st));
+        if (reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));
-        KG_TRY(launch_update(K, j, P.reorth >= 1, false, st));
-        if (P.reorth >= 2) {
+        KG_TRY(launch_update(K, j, reorth >= 1, false, st));
+        if (reorth >= 2) {
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), true, st));
             KG_TRY(launch_update(K, j, 1, true, st));
         }
     }
-    KG_TRY(launch_tridiag(K, 0, P.tau, st));
-    KG_TRY(launch_combine(K, K.V, K.colV(), P.ov, P.n_ov, P.ov_stride, P.ov_out, P.ov_rows, true, st));
+    KG_TRY(launch_tridiag(K, 0, st));
+    KG_TRY(launch_combine(K, st));
     return KG_OK;
 }
 
@@ -597,14 +656,14 @@ int enqueue_step(const StepPlan& P, cudaStream_t st) {
 int ground_state(kg_sector* s, const kg_opts* o) {
     cudaStream_t st = pick_stream(s, o);
     const int d = (int)s->d;
-    const int M = std::max(1, std::min(o->M_gs, d));
     if (o->M_gs < 2 || o->M_gs > kMaxMgs) {
         set_error("M_gs must be in [2, %d]", kMaxMgs);
         return KG_EINVAL;
     }
+    const int M = std::max(1, std::min(o->M_gs, d));
     if (!s->gs) KG_CUDA(cudaMalloc(&s->gs, sizeof(double2) * d));
     Krylov K;
-    int rc = krylov_alloc(K, 1, M, d, s->nsm);
+    int rc = krylov_alloc(K, {s}, M, s->nsm, o->schedule != 1);
     if (rc != KG_OK) {
         krylov_free(K);
         return rc;
@@ -613,14 +672,20 @@ int ground_state(kg_sector* s, const kg_opts* o) {
         krylov_free(K);
         return r;
     };
+    K.hdesc[0].out = s->gs;  // the Ritz vector of each restart goes to the cache
+    rc = krylov_upload(K, st);
     const SecView S = s->view();
-    rc = launch_random_start(K.V, d, o->seed, st);
+    double2* V0 = K.vec(0, 0);
+    double2* W0 = K.hdesc[0].W;
+    double* part = K.hdesc[0].part;
+    const int nrq = std::max(1, std::min(K.hdesc[0].nblk_max, (d + kThreads - 1) / kThreads));
+    if (rc == KG_OK) rc = launch_random_start(V0, d, o->seed, st);
     ColScalars h;
     bool converged = false;
     for (int r = 0; rc == KG_OK && r < o->max_restarts; ++r) {
         if ((rc = launch_colnorm(K, st)) != KG_OK) break;
         for (int j = 0; j < M && rc == KG_OK; ++j) {
-            rc = launch_lanczos_hpsi(S, K, j, o->schedule != 1, st);
+            rc = launch_lanczos_hpsi(K, j, st);
             for (int k0 = 0; rc == KG_OK && k0 <= j; k0 += kChunk)
                 rc = launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st);
             if (rc == KG_OK) rc = launch_update(K, j, 1, false, st);
@@ -630,8 +695,8 @@ int ground_state(kg_sector* s, const kg_opts* o) {
                 if (rc == KG_OK) rc = launch_update(K, j, 1, true, st);
             }
         }
-        if (rc == KG_OK) rc = launch_tridiag(K, 1, 0.0, st);
-        if (rc == KG_OK) rc = launch_combine(K, s->gs, 0, nullptr, 0, 0, nullptr, 0, false, st);
+        if (rc == KG_OK) rc = launch_tridiag(K, 1, st);
+        if (rc == KG_OK) rc = launch_combine(K, st);
         if (rc != KG_OK) break;
         if (cudaMemcpyAsync(&h, K.cs, sizeof(ColScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
@@ -644,10 +709,10 @@ int ground_state(kg_sector* s, const kg_opts* o) {
             break;
         }
         if ((rc = launch_scale_copy(s->gs, s->gs, d, 1.0 / h.ovnorm, st)) != KG_OK) break;
-        if ((rc = launch_hpsi(S, s->gs, K.W, st)) != KG_OK) break;
-        k_rq<<<K.nblk, kThreads, 0, st>>>(s->gs, K.W, d, K.cs, 0, K.part, K.cnt, K.nblk);
+        if ((rc = launch_hpsi(S, s->gs, W0, st)) != KG_OK) break;
+        k_rq<<<nrq, kThreads, 0, st>>>(s->gs, W0, d, K.cs, 0, part, K.cnt);
         count_launch();
-        k_rq<<<K.nblk, kThreads, 0, st>>>(s->gs, K.W, d, K.cs, 1, K.part, K.cnt, K.nblk);
+        k_rq<<<nrq, kThreads, 0, st>>>(s->gs, W0, d, K.cs, 1, part, K.cnt);
         count_launch();
         if (cudaGetLastError() != cudaSuccess) {
             rc = KG_ECUDA;
@@ -671,7 +736,7 @@ int ground_state(kg_sector* s, const kg_opts* o) {
             break;
         }
         // restart from the Ritz vector
-        if (cudaMemcpyAsync(K.V, s->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        if (cudaMemcpyAsync(V0, s->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
             rc = KG_ECUDA;
             break;
         }

@@ -16,7 +16,7 @@ namespace kg {
 template <int NX>
 __global__ void __launch_bounds__(kThreads) k_inner(const double2* __restrict__ X, int n_x,
                                                     const double2* __restrict__ Y, int d, double* part,
-                                                    unsigned* cnt, int pstride, double2* G) {
+                                                    unsigned* cnt, int pstride, double2* G, int g_stride) {
     __shared__ double sm[(kThreads / 32) * 2 * NX];
     __shared__ double bs[2 * NX], red[2 * NX];
     const int b = blockIdx.y;
@@ -36,27 +36,27 @@ __global__ void __launch_bounds__(kThreads) k_inner(const double2* __restrict__ 
         }
     }
     block_sum<2 * NX>(acc, 2 * n_x, sm, bs);
-    if (grid_finish(bs, 2 * n_x, part + (size_t)b * pstride, cnt + b, 0, red)) {
+    if (grid_finish(bs, 2 * n_x, part + (size_t)b * pstride, cnt + b, blockIdx.x, gridDim.x, red)) {
         for (int a = threadIdx.x; a < n_x; a += blockDim.x)
-            G[(size_t)b * n_x + a] = make_double2(red[2 * a], red[2 * a + 1]);
+            G[(size_t)b * g_stride + a] = make_double2(red[2 * a], red[2 * a + 1]);
     }
 }
 
 // Launches k_inner with `per_col` blocks per column over the given scratch
 // (partials: n_y rows of per_col*kPart doubles; counters: n_y, all zero).
 static int launch_inner(const double2* X, int n_x, const double2* Y, int n_y, int d, int per_col, double* part,
-                        unsigned* cnt, double2* G, cudaStream_t st) {
+                        unsigned* cnt, double2* G, int g_stride, cudaStream_t st) {
     ProfScope ps("inner", st);
     const dim3 grid(per_col, n_y);
     const int pst = per_col * kPart;
     if (n_x <= 4)
-        k_inner<4><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G);
+        k_inner<4><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G, g_stride);
     else if (n_x <= 8)
-        k_inner<8><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G);
+        k_inner<8><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G, g_stride);
     else if (n_x <= 16)
-        k_inner<16><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G);
+        k_inner<16><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G, g_stride);
     else
-        k_inner<32><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G);
+        k_inner<32><<<grid, kThreads, 0, st>>>(X, n_x, Y, d, part, cnt, pst, G, g_stride);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -108,19 +108,24 @@ static int inner_scratch(int dev, size_t part_len, size_t cnt_len, InnerScratch*
     return KG_OK;
 }
 
-}  // namespace kg
-
-extern "C" int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
-                           void* stream) {
-    using namespace kg;
-    KG_TRY(check_inner_args(X_dev, n_x, Y_dev, n_y, d, G_dev));
+int launch_inner_lib(const double2* X, int n_x, const double2* Y, int n_y, int d, double2* G, int g_stride,
+                     cudaStream_t st) {
+    KG_TRY(check_inner_args(X, n_x, Y, n_y, d, G));
     const int per_col = blocks_per_column(n_y, d);
     int dev = 0;
     KG_CUDA(cudaGetDevice(&dev));
     InnerScratch* s = nullptr;
     KG_TRY(inner_scratch(dev, (size_t)n_y * per_col * kPart, (size_t)n_y, &s));
-    return launch_inner(reinterpret_cast<const double2*>(X_dev), n_x, reinterpret_cast<const double2*>(Y_dev), n_y,
-                        (int)d, per_col, s->part, s->cnt, reinterpret_cast<double2*>(G_dev), (cudaStream_t)stream);
+    return launch_inner(X, n_x, Y, n_y, d, per_col, s->part, s->cnt, G, g_stride, st);
+}
+
+}  // namespace kg
+
+extern "C" int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
+                           void* stream) {
+    using namespace kg;
+    return launch_inner_lib(reinterpret_cast<const double2*>(X_dev), n_x, reinterpret_cast<const double2*>(Y_dev), n_y,
+                            (int)d, reinterpret_cast<double2*>(G_dev), n_x, (cudaStream_t)stream);
 }
 
 // ------------------------------------------- no-allocation variant
@@ -185,5 +190,5 @@ extern "C" int kg_overlaps_noalloc(const double* X_dev, int n_x, const double* Y
     k_noalloc_clear<<<1, kNoAllocCols, 0, st>>>();
     KG_LAUNCHED();
     return launch_inner(reinterpret_cast<const double2*>(X_dev), n_x, reinterpret_cast<const double2*>(Y_dev), n_y,
-                        (int)d, per_col, p.part, p.cnt, reinterpret_cast<double2*>(G_dev), st);
+                        (int)d, per_col, p.part, p.cnt, reinterpret_cast<double2*>(G_dev), n_x, st);
 }

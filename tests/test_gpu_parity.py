@@ -277,6 +277,60 @@ def test_hubbard_atom_on_gpu():
         assert np.max(np.abs(Gg - rg)) < 1e-13 and np.max(np.abs(Gl - rl)) < 1e-13
 
 
+# ------------------------------------------------ a9: batched instances
+def batch_models():
+    """Star SIAM instances of different sizes and fillings (c4-like) plus edge
+    cases: a full up band (no particle part) and a one-site sector."""
+    rng = np.random.default_rng(77)
+    out = []
+    for L in (6, 7, 8, 9, 5, 10):
+        nu, nd = int(rng.integers(1, L)), int(rng.integers(1, L))
+        U = float(rng.uniform(1, 8))
+        out.append(W.siam_star(-U / 2, U, rng.uniform(-3, 3, L - 1), rng.uniform(0.2, 1.0, L - 1), nu, nd))
+    out.append(W.siam_star(-1.0, 2.0, [0.5, -0.5], [0.4, 0.6], 3, 1))     # N_up = L
+    out.append(W.make_model(1, 1, 0, np.zeros((1, 1)), [[-0.3], [0.2]], [1.5]))  # d = 1
+    return out
+
+
+def test_batched_equilibrium_parity():
+    models = batch_models()
+    secs = [kg.Sector(m) for m in models]
+    orbs = [(0, 0), (0, 1)]
+    dt, n = 0.05, 60
+    Gg, Gl, status = kg.kg_green_equilibrium_batched([s.handle for s in secs], orbs, dt, n)
+    assert np.all(status == 0), status
+    for i, m in enumerate(models):
+        rg, rl, _ = oracle.green_equilibrium(m, orbs, dt, n)
+        assert np.max(np.abs(Gg[i] - rg)) < G_TOL, i
+        assert np.max(np.abs(Gl[i] - rl)) < G_TOL, i
+        # the plain per-instance path gives the same numbers
+        pg, pl = kg.Sector(m).green_equilibrium(orbs, dt, n)
+        assert np.max(np.abs(Gg[i] - pg)) < 1e-12 and np.max(np.abs(Gl[i] - pl)) < 1e-12, i
+    assert np.all(Gg[6, :, 0, 0] == 0)  # full up band: no particle part
+
+
+def test_batched_c4_subset():
+    cfg = W.config_c4()
+    models = cfg["models"][:24]
+    secs = [kg.Sector(m) for m in models]
+    Gg, Gl, status = kg.kg_green_equilibrium_batched([s.handle for s in secs], cfg["orbitals"], cfg["dt"], 20,
+                                                     kg.kg_opts_default(M=cfg["M"]))
+    checked = 0
+    for i, m in enumerate(models):
+        if status[i] != 0:
+            assert status[i] in (kg.KG_EDEGEN,), status[i]
+            continue
+        if math.comb(m["L"], m["n_up"]) * math.comb(m["L"], m["n_dn"]) > 60000:
+            continue  # oracle time; the larger ones are covered by the plain-path comparison below
+        rg, rl, _ = oracle.green_equilibrium(m, cfg["orbitals"], cfg["dt"], 20)
+        assert np.max(np.abs(Gg[i] - rg)) < G_TOL and np.max(np.abs(Gl[i] - rl)) < G_TOL, i
+        checked += 1
+    assert checked >= 12
+    big = int(np.argmax([math.comb(m["L"], m["n_up"]) * math.comb(m["L"], m["n_dn"]) for m in models]))
+    pg, pl = kg.Sector(models[big]).green_equilibrium(cfg["orbitals"], cfg["dt"], 20, kg.kg_opts_default(M=cfg["M"]))
+    assert np.max(np.abs(Gg[big] - pg)) < 1e-12 and np.max(np.abs(Gl[big] - pl)) < 1e-12
+
+
 # ------------------------------------------------------------- Keldysh G
 def keldysh_case():
     ini = W.siam_chain(6, 2.0, 3, 3, field=0.3)
