@@ -84,7 +84,7 @@ typedef struct kg_opts {
 
 void kg_opts_default(kg_opts* o);
 
-/* ---- a1: sector basis and ranking ------------------------------------------
+/* ---- sector basis and ranking ------------------------------------------
  * Builds the (L, n_up, n_dn) sector of H (Section 2, occupation-number basis
  * with N and S_z conserved) on the device: the spin strings by unranking in
  * the combinatorial number system, the per-spin hop tables (source rank and
@@ -109,7 +109,7 @@ int kg_sector_dims(const kg_sector* s, long long* dim, long long* D_up, long lon
  * of D_up and D_dn entries: the device result of the combinatorial unranking. */
 int kg_sector_strings(const kg_sector* s, unsigned int* up_host, unsigned int* dn_host);
 
-/* ---- a2: H*psi --------------------------------------------------------------
+/* ---- H*psi --------------------------------------------------------------
  * y = H x on the device (Section 2, the matrix H_jj' applied on the fly:
  * hopping by bit flips with popcount fermion signs, diagonal eps and U).
  * x_dev, y_dev: complex vectors of dimension d, must not overlap.
@@ -117,7 +117,7 @@ int kg_sector_strings(const kg_sector* s, unsigned int* up_host, unsigned int* d
  * Asynchronous (stream-ordered). */
 int kg_hpsi(kg_sector* s, const double* x_dev, double* y_dev, void* stream);
 
-/* ---- a6: c / c^dag sector maps ------------------------------------------
+/* ---- c / c^dag sector maps ------------------------------------------
  * y = c_{site,spin} x (dagger = 0) or y = c^dag_{site,spin} x (dagger = 1),
  * mapping sector (N_up, N_dn) to the neighbouring sector with N_spin -/+ 1
  * (Section 3, the state c^dag_a' |0> of Eq. (psit); Section 4, step (iii)).
@@ -128,7 +128,7 @@ int kg_neighbour_dim(kg_sector* s, int spin, int dagger, long long* dim);
 int kg_apply_cop(kg_sector* s, int site, int spin, int dagger, const double* x_dev, double* y_dev,
                  void* stream);
 
-/* ---- a7: overlaps of caller-held vectors -----------------------------------
+/* ---- overlaps of caller-held vectors -----------------------------------
  * G[b][a] = <x_a | y_b> = sum_i conj(x_a[i]) y_b[i] for the n_x vectors
  * X_dev (complex, [n_x][d] row-major) and the n_y vectors Y_dev ([n_y][d]):
  * the inner products from which the Green's functions are assembled
@@ -155,7 +155,7 @@ int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long
 int kg_overlaps_noalloc(const double* X_dev, int n_x, const double* Y_dev, int n_y, long long d, double* G_dev,
                         void* stream);
 
-/* ---- a3-a5: ground state -------------------------------------------------
+/* ---- ground state -------------------------------------------------
  * Lanczos ground state of the sector (Section 2: recursion Eq. (recursion)
  * with full reorthogonalisation, T of Eq. (tmatrix) diagonalised on the
  * device, Eq. (tdiag), Ritz vector Eq. (eigen)), restarted from the Ritz
@@ -171,7 +171,7 @@ int kg_ground_state(kg_sector* s, const kg_opts* o, double* E0, double* resid, d
  * kg_ground_state. */
 int kg_copy_ground_state(kg_sector* s, double* psi, int to_host);
 
-/* ---- a3-a5: Krylov propagation ------------------------------------------
+/* ---- Krylov propagation ------------------------------------------
  * x <- exp(-i H dt)^n_steps x in place on the device (Section 3, Eqs.
  * (newstate) and (udelta): one Lanczos space of dimension opts->M per step,
  * T diagonalised on the device, exp(-i D dt) applied in the small space,
@@ -179,7 +179,7 @@ int kg_copy_ground_state(kg_sector* s, double* psi, int to_host);
  * backward, exp(+i H |dt|).  Returns when x_dev holds the result. */
 int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_opts* o);
 
-/* ---- a7 + driver: equilibrium Green's function ---------------------------
+/* ---- equilibrium Green's function ---------------------------
  * Section 3, Eqs. (psit)/(psigreen) with eta = 0, and the hole part given
  * after Eq. (gomega); for t_k = k*dt, k = 0..n_steps:
  *   G_gtr[k][a][a'] = -i e^{+i E0 t_k} <c^dag_a 0| e^{-iH t_k} |c^dag_a' 0>
@@ -190,7 +190,7 @@ int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_o
 int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps,
                          const kg_opts* o, double* G_gtr, double* G_les);
 
-/* ---- a9: batched equilibrium Green's functions ----------------------------
+/* ---- batched equilibrium Green's functions ----------------------------
  * The equilibrium Green's functions of n_inst independent sectors (for
  * example the repeated impurity solves of DMFT/VCA-type embedding schemes,
  * Section 1), computed together: after each instance's ground state, the
@@ -206,7 +206,30 @@ int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int
 int kg_green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt,
                                  int n_steps, const kg_opts* o, double* G_gtr, double* G_les, int* status);
 
-/* ---- a8: nonequilibrium (Keldysh) Green's function -----------------------
+/* ---- adjoint of the equilibrium Green's function ----------------------
+ * Vector-Jacobian product of kg_green_equilibrium with respect to the
+ * Hamiltonian parameters (not in the paper; built on the structure of its
+ * propagation, Section 3).  For a real loss L of the returned G, the caller
+ * passes the cotangents dG_gtr, dG_les (host, complex [n_steps+1][n_orb]
+ * [n_orb], entry = dL/dRe G + i dL/dIm G; either may be NULL = zero) and
+ * receives, on the host,
+ *   g_eps[sigma*L + i] = dL/d eps_{i sigma},     g_U[i] = dL/dU_i,
+ *   g_hre[i*L + j] = dL/dRe h_ij  (h_ji = conj(h_ij) tied, so symmetric;
+ *                    the diagonal is dL/dh_ii = sum over spins of g_eps),
+ *   g_him[i*L + j] = dL/dIm h_ij  (antisymmetric).
+ * Method: adjoint states propagated backward with the same Krylov steps,
+ * Frechet derivative of each step by 10-point Gauss-Legendre quadrature with
+ * node vectors from that step's Krylov spaces, ground-state terms by
+ * Hellmann-Feynman and one projected conjugate-gradient solve.  Forward
+ * states are checkpointed every `checkpoint` steps (0 = 20) and recomputed.
+ * The quadrature is exact to rounding when |dt| times the spectral width of
+ * the sectors is below about 3.  Other arguments as for
+ * kg_green_equilibrium. */
+int kg_green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
+                             int checkpoint, const double* dG_gtr, const double* dG_les, double* g_eps,
+                             double* g_hre, double* g_him, double* g_U);
+
+/* ---- nonequilibrium (Keldysh) Green's function -----------------------
  * Section 4, steps (i)-(iv): |0> = ground state of H_ini; Phi(t) =
  * e^{-iH t}|0> with H = H_fin; Psi_a(t) = e^{iHt} c_a Phi(t) and
  * chi_a(t) = e^{iHt} c^dag_a Phi(t); then for t_k = k*dt, k < n_t,

@@ -65,6 +65,7 @@ _sig = {
     "kg_green_equilibrium": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_keldysh": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_equilibrium_batched": (_I, [_P, _I, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P, _P]),
+    "kg_green_equilibrium_vjp": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _I, _P, _P, _P, _P, _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -221,6 +222,26 @@ def kg_green_equilibrium_batched(handles, orbitals, dt, n_steps, opts=None):
                                             int(n_steps), ctypes.byref(o), Gg.ctypes.data, Gl.ctypes.data,
                                             status.ctypes.data), "kg_green_equilibrium_batched")
     return Gg, Gl, status
+
+
+def kg_green_equilibrium_vjp(handle, L, orbitals, dt, n_steps, dG_gtr=None, dG_les=None, opts=None, checkpoint=0):
+    """Gradients (g_eps [2, L], g_hre [L, L], g_him [L, L], g_U [L]) of a loss
+    whose cotangents with respect to G^> and G^< are dG_gtr, dG_les."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    shape = (n_steps + 1, n, n)
+    dg = None if dG_gtr is None else np.ascontiguousarray(np.asarray(dG_gtr, dtype=np.complex128).reshape(shape))
+    dl = None if dG_les is None else np.ascontiguousarray(np.asarray(dG_les, dtype=np.complex128).reshape(shape))
+    g_eps = np.zeros((2, L))
+    g_hre = np.zeros((L, L))
+    g_him = np.zeros((L, L))
+    g_U = np.zeros(L)
+    _check(lib.kg_green_equilibrium_vjp(handle, orb.ctypes.data, n, float(dt), int(n_steps), ctypes.byref(o),
+                                        int(checkpoint), None if dg is None else dg.ctypes.data,
+                                        None if dl is None else dl.ctypes.data, g_eps.ctypes.data, g_hre.ctypes.data,
+                                        g_him.ctypes.data, g_U.ctypes.data), "kg_green_equilibrium_vjp")
+    return g_eps, g_hre, g_him, g_U
 
 
 def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):

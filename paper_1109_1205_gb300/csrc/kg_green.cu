@@ -1,4 +1,4 @@
-// kg_green.cu -- a7/a8/a9: the Green's-function drivers.
+// kg_green.cu -- the Green's-function drivers.
 //
 // Equilibrium (Section 3, Eqs. (psit), (psigreen), eta = 0; hole part after
 // Eq. (gomega)):  the columns c^dag_a'|0> (particle) and c_a|0> (hole) are
@@ -333,7 +333,7 @@ int green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, i
     return green_eq_batch(s, n_inst, orb, n_orb, dt, n_steps, o, G_gtr, G_les, status, true);
 }
 
-// --------------------------------------------------- a7: Gram, step (iv)
+// --------------------------------------------------- Gram, step (iv)
 // G[p][q] = <X_p | X_q> for the upper-triangle tiles (p tile <= q tile) of a
 // set of nv vectors of dimension d, FP64 on the CUDA cores.  32 x 32 output
 // tile per block, 2 x 2 complex outputs per thread, 16-element slabs of the

@@ -1,4 +1,4 @@
-// kg_hpsi.cu -- a2: the Hamiltonian applied on the fly in the
+// kg_hpsi.cu -- the Hamiltonian applied on the fly in the
 // occupation-number basis (Section 2, H_jj'; model Hamiltonians of Sections 3
 // and 4).  One thread produces one output element y[s], s = i_dn*D_up + i_up:
 //

@@ -178,28 +178,31 @@ void krylov_free(Krylov& K);
 int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n);
 
 // ----------------------------------------------------------- launchers
-// a2: y = H x (plain).
+// y = H x (plain).
 int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st);
-// a2+a3: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
+// Lanczos H*psi: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
 // partial sums of a_j = <v_j, w> reduced on the device.
 int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st);
 // start of a step: beta0 = ||V_0||, scale[0], largest exponent, m_eff = M.
 int launch_colnorm(Krylov& K, cudaStream_t st);
-// a3 reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or
+// Reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or
 // h_k = <v_k, V_{j+1}> (second pass) for k in [k0, k0 + nk).
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st);
-// a3 update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
+// Lanczos update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
 // second pass), then b_{j+1} = ||V_{j+1}||, scale, breakdown test.
 int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st);
-// a4: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1
+// Tridiagonal step: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1
 // with each column's tau; mode 1: ground-state Ritz pair (lam0, c = q_0).
 int launch_tridiag(Krylov& K, int mode, cudaStream_t st);
-// a5 + a7: out = sum_k c_k V_k per column; ||out||; overlaps <ov_a, out>.
+// The same for several times at once: cq[b][t][k] = coefficients of
+// exp(-i H taus[b][t]) v_0 in the stored basis (adjoint quadrature nodes).
+int launch_tridiag_multi(Krylov& K, const double* taus, int ntau, double2* cq, cudaStream_t st);
+// Combination and overlaps: out = sum_k c_k V_k per column; ||out||; overlaps <ov_a, out>.
 int launch_combine(Krylov& K, cudaStream_t st);
-// a7: G[b*g_stride + a] = <x_a | y_b> (kg_overlap.cu), library scratch.
+// Overlaps: G[b*g_stride + a] = <x_a | y_b> (kg_overlap.cu), library scratch.
 int launch_inner_lib(const double2* X, int n_x, const double2* Y, int n_y, int d, double2* G, int g_stride,
                      cudaStream_t st);
-// a6: y = c / c^dag x between neighbouring sectors.
+// y = c / c^dag x between neighbouring sectors.
 int launch_cop(const kg_sector* src, const kg_sector* dst, int site, int spin, int dagger,
                const double2* x, double2* y, cudaStream_t st);
 // utilities
@@ -215,7 +218,7 @@ cudaStream_t pick_stream(const kg_sector* s, const kg_opts* o);
 
 // One propagation step exp(-i H tau_b) of every column b of K, starting from
 // V[b][0] and leaving the result at desc[b].out (V[b][0] unless changed),
-// with the overlaps configured in the column descriptors (a2-a5, a7).
+// with the overlaps configured in the column descriptors.
 int enqueue_step(Krylov& K, int reorth, cudaStream_t st);
 // Builds every work list a step uses (device allocations) so that the step
 // can then be captured into a graph, where allocation is not allowed.
@@ -244,6 +247,9 @@ int green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_
 int green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
                               const kg_opts* o, double* G_gtr, double* G_les, int* status);
 int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<double>>& G, cudaStream_t st);
+int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
+                          int checkpoint, const double* dGgtr, const double* dGles, double* g_eps, double* g_hre,
+                          double* g_him, double* g_U);
 int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                    const kg_opts* o, kg_keldysh** out);
 void keldysh_free(kg_keldysh* X);

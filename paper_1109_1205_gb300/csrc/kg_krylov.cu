@@ -1,4 +1,4 @@
-// kg_krylov.cu -- a3-a5: the Lanczos recursion with full
+// kg_krylov.cu -- the Lanczos recursion with full
 // reorthogonalisation, the small tridiagonal eigenproblem and exponential,
 // and the basis combination (Section 2, Eqs. (recursion), (tmatrix),
 // (tdiag), (eigen); Section 3, Eqs. (newstate) and (udelta)).
@@ -182,7 +182,7 @@ int launch_colnorm(Krylov& K, cudaStream_t st) {
     return KG_OK;
 }
 
-// ---------------------------------------- a3: Gram-Schmidt coefficients
+// ---------------------------------------- Gram-Schmidt coefficients
 // First pass:  u = W - a_j v_j,  h_k = <v_k, u>   for k in [k0, k0+nk)
 // Second pass: u = V_{j+1},      h_k = <v_k, u>
 // NK (compile time) bounds nk so that the accumulators stay in registers
@@ -247,7 +247,7 @@ int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream
     return KG_OK;
 }
 
-// ------------------------------------------------------ a3: the update
+// ------------------------------------------------------ the update
 // First pass:  V_{j+1} = W - a_j v_j - [reorth] sum_{k<=j} h_k v_k
 // Second pass: V_{j+1} -= sum_{k<=j} h_k v_k
 // then b_{j+1} = ||V_{j+1}||, s_{j+1} = 1/b_{j+1}, a_j += Re h_j, the
@@ -349,7 +349,7 @@ int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
     return KG_OK;
 }
 
-// ------------------------------------------- a4: tridiagonal eigenproblem
+// ------------------------------------------- tridiagonal eigenproblem
 // One warp per column.  Implicit symmetric QR with Wilkinson shifts on the
 // unreduced blocks of T (Golub and Van Loan, Section 8.3): lane 0 chases the
 // bulge and records the Givens rotations of one sweep in shared memory, then
@@ -363,7 +363,8 @@ int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
 constexpr int kTriWarps = 4;
 
 __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc, ColScalars* cs, int B, int Mcap,
-                                                           double* Qall, int mode) {
+                                                           double* Qall, int mode, const double* taus, int ntau,
+                                                           double2* cq) {
     __shared__ double sd[kTriWarps][kMaxMgs], se[kTriWarps][kMaxMgs];
     __shared__ double rc[kTriWarps][kMaxMgs], rs[kTriWarps][kMaxMgs];
     __shared__ int ctl[kTriWarps][4];
@@ -455,27 +456,40 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
     }
     if (lane == 0 && iter >= max_iter) C->status = KG_ENOCONV;
     __syncwarp();
-    if (mode == 0) {
+    if (mode == 0 || mode == 2) {
+        // mode 0: the column's own tau into C->c; mode 2: ntau times
+        // (quadrature nodes) into cq[b][t][k], from the same diagonalisation
         const double beta0 = C->beta0;
         double* pc = rc[warp];  // rotation buffers are free now: phases of e^{-i lambda tau}
         double* ps = rs[warp];
-        for (int mm = lane; mm < m; mm += 32) {
-            double sn, cn;
-            sincos(d[mm] * tau, &sn, &cn);
-            pc[mm] = cn * Q[mm];  // Q[0][mm] is Q[mm]
-            ps[mm] = sn * Q[mm];
-        }
-        __syncwarp();
-        for (int k = lane; k < m; k += 32) {
-            double re = 0.0, im = 0.0;
-            for (int mm = 0; mm < m; ++mm) {
-                const double q = Q[(size_t)k * m + mm];
-                re = fma(q, pc[mm], re);
-                im = fma(-q, ps[mm], im);
+        const int nt = mode == 0 ? 1 : ntau;
+        for (int t = 0; t < nt; ++t) {
+            const double tt = mode == 0 ? tau : taus[(size_t)b * ntau + t];
+            __syncwarp();
+            for (int mm = lane; mm < m; mm += 32) {
+                double sn, cn;
+                sincos(d[mm] * tt, &sn, &cn);
+                pc[mm] = cn * Q[mm];  // Q[0][mm] is Q[mm]
+                ps[mm] = sn * Q[mm];
             }
-            const double s = beta0 * C->scale[k];
-            C->c[k] = make_double2(s * re, s * im);
+            __syncwarp();
+            for (int k = lane; k < m; k += 32) {
+                double re = 0.0, im = 0.0;
+                for (int mm = 0; mm < m; ++mm) {
+                    const double q = Q[(size_t)k * m + mm];
+                    re = fma(q, pc[mm], re);
+                    im = fma(-q, ps[mm], im);
+                }
+                const double s = beta0 * C->scale[k];
+                if (mode == 0)
+                    C->c[k] = make_double2(s * re, s * im);
+                else
+                    cq[((size_t)b * ntau + t) * Mcap + k] = make_double2(s * re, s * im);
+            }
         }
+        if (mode == 2)
+            for (int t = 0; t < ntau; ++t)
+                for (int k = m + lane; k < Mcap; k += 32) cq[((size_t)b * ntau + t) * Mcap + k] = make_double2(0.0, 0.0);
     } else {
         int m0 = 0, m1 = -1;
         for (int i = 1; i < m; ++i)
@@ -494,12 +508,12 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
 int launch_tridiag(Krylov& K, int mode, cudaStream_t st) {
     const int nb = (K.B + kTriWarps - 1) / kTriWarps;
     ProfScope ps("tridiag", st);
-    k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, mode);
+    k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, mode, nullptr, 0, nullptr);
     KG_LAUNCHED();
     return KG_OK;
 }
 
-// ----------------------------------- a5 + a7: combination and overlaps
+// ----------------------------------- combination and overlaps
 // out = sum_{k<m} c_k V_k  (Eq. (udelta) in the form V x small vector), then
 // ||out|| and <ov_a, out> for the column's n_ov overlap vectors, written to
 // row cs[b].ov_slot of its overlap table (the slot advances by one).  NOV
@@ -602,6 +616,16 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
         else
             cs->rnorm = sqrt(red[0]);
     }
+}
+
+// Coefficients of exp(-i H t) v_0 for ntau times per column (taus[b][t]),
+// into cq[b][t][0..M) (already times the scales of the stored vectors).
+int launch_tridiag_multi(Krylov& K, const double* taus, int ntau, double2* cq, cudaStream_t st) {
+    const int nb = (K.B + kTriWarps - 1) / kTriWarps;
+    ProfScope ps("tridiag", st);
+    k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, 2, taus, ntau, cq);
+    KG_LAUNCHED();
+    return KG_OK;
 }
 
 // -------------------------------------------------- step sequencing

@@ -1,4 +1,4 @@
-// kg_overlap.cu -- a7 for caller-held vectors: batched inner products
+// kg_overlap.cu -- overlaps of caller-held vectors: batched inner products
 //     G[b][a] = <x_a | y_b> = sum_i conj(x_a[i]) y_b[i]
 // the overlaps from which the Green's functions are assembled (Section 3,
 // Eq. (psigreen); Section 4, step (iv): G^<(t,t') = i <Psi_a'(t')|Psi_a(t)>).

@@ -67,7 +67,7 @@ static int upload_binomials() {
     return status;
 }
 
-// ----------------------------------------------------------- a1 kernels
+// ----------------------------------------------------------- basis kernels
 __device__ __forceinline__ uint32_t rank_string(uint32_t b) {
     uint32_t r = 0;
     int j = 1;
@@ -362,7 +362,7 @@ cudaStream_t pick_stream(const kg_sector* s, const kg_opts* o) {
     return s->stream;
 }
 
-// --------------------------------------------------------- a6: c / c^dag
+// --------------------------------------------------------- c / c^dag
 // Target-side gather: every element of the destination sector looks up the
 // one source element it can come from.
 __global__ void k_cop(int L, int site, int spin, int dagger, int nu_src, int Du_dst, int d_dst, int Du_src,

@@ -42,7 +42,7 @@ def relerr(a, b):
     return np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b)))
 
 
-# --------------------------------------------------------------- a1 ranking
+# --------------------------------------------------------------- ranking
 @pytest.mark.parametrize("L,nu,nd", [(1, 0, 1), (6, 3, 2), (12, 6, 6), (16, 7, 8), (20, 3, 17)])
 def test_strings_are_rank_ordered(L, nu, nd):
     s = kg.Sector(W.hubbard_ring(L, 1.0, nu, nd))
@@ -58,7 +58,7 @@ def test_strings_are_rank_ordered(L, nu, nd):
     assert s.dim == math.comb(L, nu) * math.comb(L, nd)
 
 
-# ------------------------------------------------------------------ a2 H*psi
+# ------------------------------------------------------------------ H*psi
 HPSI_MODELS = [
     ("complex", W.random_model(6, 3, 2, seed=1, complex_hopping=True)),
     ("real-nonuniform", W.random_model(8, 4, 3, seed=2, complex_hopping=False, density=0.6)),
@@ -95,7 +95,7 @@ def test_hpsi_linearity_and_hermiticity():
     assert abs(np.vdot(z, hx) - np.vdot(hz, x)) < 1e-12
 
 
-# ------------------------------------------------------------ a6 c / c^dag
+# ------------------------------------------------------------ c / c^dag
 def test_cop_bit_exact():
     m = W.random_model(6, 3, 2, seed=9, complex_hopping=True)
     s = kg.Sector(m)
@@ -122,7 +122,7 @@ def test_cop_missing_neighbour_is_einval():
         s.neighbour_dim(1, False)  # N_dn = 0: nothing to annihilate
 
 
-# ------------------------------------------------------- a7 overlaps
+# ------------------------------------------------------- overlaps
 @pytest.mark.parametrize("n_x,n_y,d", [(1, 1, 1), (3, 5, 1000), (12, 12, 731808), (32, 40, 4097), (17, 1, 300001)])
 def test_overlaps_parity(n_x, n_y, d):
     rng = np.random.default_rng(n_x * 1000 + n_y)
@@ -148,7 +148,7 @@ def test_overlaps_rejects_bad_sizes():
         assert e.value.code == kg.KG_EINVAL
 
 
-# ---------------------------------------------------------- a3-a5 ground state
+# ---------------------------------------------------------- ground state
 GS_MODELS = [
     ("c1", W.config_c1()["model"]),
     ("complex-L7", W.random_model(7, 3, 4, seed=5, complex_hopping=True)),
@@ -277,7 +277,7 @@ def test_hubbard_atom_on_gpu():
         assert np.max(np.abs(Gg - rg)) < 1e-13 and np.max(np.abs(Gl - rl)) < 1e-13
 
 
-# ------------------------------------------------ a9: batched instances
+# ------------------------------------------------ batched instances
 def batch_models():
     """Star SIAM instances of different sizes and fillings (c4-like) plus edge
     cases: a full up band (no particle part) and a one-site sector."""
