@@ -13,6 +13,8 @@
 // coefficients) never leave the device: a whole propagation step is a fixed
 // launch sequence that a CUDA graph can replay.
 #include <algorithm>
+#include <array>
+#include <utility>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -227,22 +229,31 @@ __global__ void __launch_bounds__(kThreads) k_reorth_dots(const ColDesc* desc, c
     }
 }
 
+// The accumulators of k_reorth_dots are compile-time sized.  A kernel built
+// for more vectors than a launch needs would still issue the FP64 multiply-adds
+// of the unused slots (predicated off, but occupying the FP64 pipe, which
+// bounds this kernel), so every count up to 24 has its own instantiation;
+// 25..28 and 29..32 share one.
+using DotsKernel = void (*)(const ColDesc*, const int4*, ColScalars*, int, int, int, int, unsigned*);
+
+template <int... N>
+static constexpr std::array<DotsKernel, sizeof...(N)> dots_table(std::integer_sequence<int, N...>) {
+    return {{&k_reorth_dots<N + 1>...}};
+}
+
+static DotsKernel dots_kernel(int nk) {
+    static const std::array<DotsKernel, 24> exact = dots_table(std::make_integer_sequence<int, 24>{});
+    if (nk <= 24) return exact[nk - 1];
+    return nk <= 28 ? &k_reorth_dots<28> : &k_reorth_dots<32>;
+}
+
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
     ProfScope ps("reorth_dots", st);
-    const int sec = second ? 1 : 0;
+    const DotsKernel kern = dots_kernel(nk);
     const int4* items;
     int n;
-#define KG_DOTS(NK)                                                                         \
-    do {                                                                                    \
-        KG_TRY(work_list(K, (const void*)k_reorth_dots<NK>, -1, &items, &n));               \
-        k_reorth_dots<NK><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, k0, nk, sec, K.cnt); \
-    } while (0)
-    if (nk <= 4) KG_DOTS(4);
-    else if (nk <= 8) KG_DOTS(8);
-    else if (nk <= 16) KG_DOTS(16);
-    else if (nk <= 24) KG_DOTS(24);
-    else KG_DOTS(32);
-#undef KG_DOTS
+    KG_TRY(work_list(K, (const void*)kern, -1, &items, &n));
+    kern<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, k0, nk, second ? 1 : 0, K.cnt);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -646,10 +657,9 @@ int prepare_step(Krylov& K, int reorth) {
     KG_TRY(work_list(K, (const void*)k_colnorm, -1, &items, &n));
     KG_TRY(work_list(K, (const void*)k_update, -1, &items, &n));
     if (reorth >= 1) {
-        const void* dots[5] = {(const void*)k_reorth_dots<4>, (const void*)k_reorth_dots<8>,
-                               (const void*)k_reorth_dots<16>, (const void*)k_reorth_dots<24>,
-                               (const void*)k_reorth_dots<32>};
-        for (auto* k : dots) KG_TRY(work_list(K, k, -1, &items, &n));
+        // every vector count of one step (and of the ground-state restarts)
+        for (int nk = 1; nk <= std::min(kChunk, K.M + 1); ++nk)
+            KG_TRY(work_list(K, (const void*)dots_kernel(nk), -1, &items, &n));
     }
     const void* comb[4] = {(const void*)k_combine<0>, (const void*)k_combine<4>, (const void*)k_combine<12>,
                            (const void*)k_combine<32>};
