@@ -369,20 +369,27 @@ def run_reference(args):
 
 
 def run_ncu_case(args):
-    """Small case for full ncu captures: one column of the c2 N-1 sector
-    (d = 731,808, 0.26 GB of Krylov basis, more than the L2) propagated
-    backward by 3 Krylov steps with the benchmark's options."""
+    """Small case for full ncu captures: one Keldysh row of the c2 quench
+    restricted to 6 orbitals (two batches of 6 columns of the N-1 / N+1
+    sectors, d = 731,808, 1.5 GB of Krylov basis per batch, more than the L2),
+    backward by 2 Krylov steps with the benchmark's options.  The row runs
+    inside the NVTX range "row" so that a capture can skip the set-up."""
     import torch
 
     import paper_1109_1205_gb300 as kg
     import workloads as W
     cfg = W.config_c2()
-    sec = kg.Sector(W.with_sector(cfg["fin"], 5, 6))
-    x = torch.from_numpy(W.random_state(sec.dim, 5)).cuda()
-    sec.propagate(x, -cfg["dt"], 3, kg.kg_opts_default(M=cfg["M"], reorth=1))
+    opts = kg.kg_opts_default(M=cfg["M"], reorth=1)
+    si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+    si.ground_state(opts)
+    K = kg.Keldysh(si, sf, cfg["orbitals"][:6], cfg["dt"], 3, opts)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": "c2 N-1 column", "d": sec.dim, "launches": kg.kg_launch_count(),
-                      "norm": float(torch.linalg.vector_norm(x).item())}))
+    torch.cuda.nvtx.range_push("row")
+    Gl, Gg = K.row(2)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"ncu_case": "c2 row t_2, 6 orbitals", "d": sf.dim, "launches": kg.kg_launch_count(),
+                      "G_les_00": [float(Gl[0, 0].real), float(Gl[0, 0].imag)]}))
 
 
 def main():

@@ -17,7 +17,7 @@ namespace kg {
 constexpr int kMaxL = 32;      // spin strings are 32-bit words
 constexpr int kMaxM = 64;      // Krylov dimension of one propagation step
 constexpr int kMaxMgs = 256;   // Krylov dimension of one ground-state restart
-constexpr int kChunk = 32;     // complex dot products accumulated per pass
+constexpr int kChunk = 24;     // complex dot products accumulated per pass
 constexpr int kMaxOv = 32;     // overlap vectors fused into the combination pass
 constexpr int kPart = 72;      // doubles per block in a partial-sum row
 constexpr int kThreads = 256;  // threads per block of the streaming kernels
@@ -135,6 +135,8 @@ struct ColScalars {
 struct ColDesc {
     const SecView* sec;     // this column's sector (device copy)
     double2* V;             // [M+1][d] Lanczos vectors (unnormalised)
+    double* S;              // [M+1][d] Re + Im of each component of V_k (or null)
+    float2* V32;            // [M+1][d] V_k truncated to FP32 (or null)
     double2* W;             // [d] H v workspace
     double* part;           // [nblk_max][kPart] partial sums of this column
     double2* out;           // where the combination writes (V_0 by default)
@@ -163,6 +165,8 @@ struct Krylov {
     unsigned* cnt = nullptr;        // [B]
     double* Q = nullptr;            // [B][M*M] eigenvectors of T
     double2* Vbuf = nullptr;
+    double* Sbuf = nullptr;         // planes of the Gram-Schmidt kernels (optional)
+    float2* V32buf = nullptr;
     double2* Wbuf = nullptr;
     double* partbuf = nullptr;
     std::map<long long, std::pair<int4*, int>> lists;

@@ -55,6 +55,17 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         np += (size_t)D.nblk_max * kPart;
     }
     KG_CUDA(cudaMalloc(&K.Vbuf, sizeof(double2) * nv));
+    // Planes read by the Gram-Schmidt kernels (Re+Im for the three-multiply
+    // dot products, a truncated FP32 copy for the small correction terms).
+    // They are optional: without the memory the kernels use V alone.
+    if (cudaMalloc(&K.Sbuf, sizeof(double) * nv) != cudaSuccess ||
+        cudaMalloc(&K.V32buf, sizeof(float2) * nv) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(K.Sbuf);
+        cudaFree(K.V32buf);
+        K.Sbuf = nullptr;
+        K.V32buf = nullptr;
+    }
     KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * nw));
     KG_CUDA(cudaMalloc(&K.partbuf, sizeof(double) * np));
     KG_CUDA(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B));
@@ -69,6 +80,8 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         ColDesc& D = K.hdesc[b];
         D.sec = K.secs + b;
         D.V = K.Vbuf + ov;
+        D.S = K.Sbuf ? K.Sbuf + ov : nullptr;
+        D.V32 = K.V32buf ? K.V32buf + ov : nullptr;
         D.W = K.Wbuf + ow;
         D.part = K.partbuf + op;
         D.out = D.V;
@@ -89,6 +102,8 @@ int krylov_upload(Krylov& K, cudaStream_t st) {
 void krylov_free(Krylov& K) {
     for (auto& kv : K.lists) cudaFree(kv.second.first);
     cudaFree(K.Vbuf);
+    cudaFree(K.Sbuf);
+    cudaFree(K.V32buf);
     cudaFree(K.Wbuf);
     cudaFree(K.partbuf);
     cudaFree(K.desc);
@@ -157,6 +172,10 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(const ColDesc* desc, const
         const double2 v = x[i];
         acc[0] = fma(v.x, v.x, fma(v.y, v.y, acc[0]));
         em = max(em, max(exp_field(v.x), exp_field(v.y)));
+        if (D.S) {
+            D.S[i] = v.x + v.y;
+            D.V32[i] = make_float2(f64_to_f32_trunc(v.x), f64_to_f32_trunc(v.y));
+        }
     }
     em = block_max_int(em, smi);
     block_sum<1>(acc, 1, sm, bs);
@@ -185,55 +204,112 @@ int launch_colnorm(Krylov& K, cudaStream_t st) {
 }
 
 // ---------------------------------------- Gram-Schmidt coefficients
-// First pass:  u = W - a_j v_j,  h_k = <v_k, u>   for k in [k0, k0+nk)
+// First pass:  u = W - a_j v_j,  h_k = <v_k, u>   for k in [k0, k0+NK)
 // Second pass: u = V_{j+1},      h_k = <v_k, u>
-// NK (compile time) bounds nk so that the accumulators stay in registers
-// without holding 64 of them when only a few vectors are needed.
+//
+// With the plane S_k = Re V_k + Im V_k present, each complex product takes
+// three FP64 multiply-adds instead of four (v = a + ib, u = c + id):
+//   T1 = sum a c,  T2 = sum b d,  T3 = sum (a + b)(d - c),
+//   Re <v,u> = T1 + T2,  Im <v,u> = T3 + T1 - T2,
+// with d - c formed once per element and shared by all k.  The FP64 pipe
+// bounds this kernel, so the extra 8 bytes per element of S cost less than
+// the multiply-add they save.
+//
+// The accumulators live in registers.  For more than 12 vectors the two
+// halves of the block take the two halves of the k range over the same
+// elements (u is read twice, the second time from cache), which keeps the
+// kernel at two blocks per SM without spilling.
 template <int NK>
-__global__ void __launch_bounds__(kThreads) k_reorth_dots(const ColDesc* desc, const int4* items, ColScalars* cs,
-                                                          int j, int k0, int nk, int second, unsigned* cnt) {
-    __shared__ double sm[(kThreads / 32) * 2 * NK];
-    __shared__ double bs[2 * NK], red[2 * NK];
+__global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                             int j, int k0, int nk, int second, unsigned* cnt) {
+    constexpr int G = NK > 12 ? 2 : 1;         // thread groups splitting the k range
+    constexpr int KH = (NK + G - 1) / G;       // vectors per group
+    constexpr int TG = kThreads / G;           // threads per group
+    __shared__ double sm[(kThreads / 32) * 3 * KH];
+    __shared__ double bs[3 * NK], red[3 * NK];
     KG_ITEM();
     if (j >= C->m_eff) return;
     const int d = D.d;
-    const double2* Vb = D.V;
-    const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
-    const double2* vj = Vb + (size_t)j * d;
+    const int grp = threadIdx.x / TG, t = threadIdx.x % TG;
+    const int kb = grp * KH, kn = min(KH, NK - kb);
+    const double2* Vb = D.V + (size_t)(k0 + kb) * d;
+    const double2* w = second ? D.V + (size_t)(j + 1) * d : D.W;
+    const double2* vj = D.V + (size_t)j * d;
     const double aj = second ? 0.0 : C->alpha[j] * C->scale[j];
-    double acc[2 * NK];
+    double acc[3 * KH];
 #pragma unroll
-    for (int k = 0; k < 2 * NK; ++k) acc[k] = 0.0;
-    KG_FOR(i) {
-        double2 u = w[i];
-        if (!second) {
-            const double2 p = vj[i];
-            u.x = fma(-aj, p.x, u.x);
-            u.y = fma(-aj, p.y, u.y);
+    for (int k = 0; k < 3 * KH; ++k) acc[k] = 0.0;
+    const bool three = D.S != nullptr;
+    if (three) {
+        const double* Sb = D.S + (size_t)(k0 + kb) * d;
+        for (int i = blk * TG + t; i < d; i += nblk * TG) {
+            double2 u = w[i];
+            if (!second) {
+                const double2 p = vj[i];
+                u.x = fma(-aj, p.x, u.x);
+                u.y = fma(-aj, p.y, u.y);
+            }
+            const double dmc = u.y - u.x;
+#pragma unroll
+            for (int k = 0; k < KH; ++k) {
+                if (k < kn) {
+                    const size_t o = (size_t)k * d + i;
+                    const double2 v = Vb[o];
+                    const double sv = Sb[o];
+                    acc[3 * k] = fma(v.x, u.x, acc[3 * k]);
+                    acc[3 * k + 1] = fma(v.y, u.y, acc[3 * k + 1]);
+                    acc[3 * k + 2] = fma(sv, dmc, acc[3 * k + 2]);
+                }
+            }
         }
+    } else {
+        for (int i = blk * TG + t; i < d; i += nblk * TG) {
+            double2 u = w[i];
+            if (!second) {
+                const double2 p = vj[i];
+                u.x = fma(-aj, p.x, u.x);
+                u.y = fma(-aj, p.y, u.y);
+            }
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            if (k < nk) {
-                const double2 v = Vb[(size_t)(k0 + k) * d + i];
-                acc[2 * k] = fma(v.x, u.x, fma(v.y, u.y, acc[2 * k]));
-                acc[2 * k + 1] = fma(v.x, u.y, fma(-v.y, u.x, acc[2 * k + 1]));
+            for (int k = 0; k < KH; ++k) {
+                if (k < kn) {
+                    const double2 v = Vb[(size_t)k * d + i];
+                    acc[3 * k] = fma(v.x, u.x, fma(v.y, u.y, acc[3 * k]));
+                    acc[3 * k + 1] = fma(v.x, u.y, fma(-v.y, u.x, acc[3 * k + 1]));
+                }
             }
         }
     }
-    block_sum<2 * NK>(acc, 2 * nk, sm, bs);
-    if (grid_finish(bs, 2 * nk, D.part, cnt + b, blk, nblk, red)) {
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    // block sums: warps reduce their accumulators, then each group's warps
+    // are added in warp order (fixed order, so results are reproducible)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3 * KH; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sm[warp * 3 * KH + k] = v;
+    }
+    __syncthreads();
+    constexpr int WG = TG / 32;  // warps per group
+    for (int q = threadIdx.x; q < 3 * NK; q += blockDim.x) {
+        const int g = q / (3 * KH), l = q - g * 3 * KH;
+        double s = 0.0;
+        for (int w2 = 0; w2 < WG; ++w2) s += sm[(g * WG + w2) * 3 * KH + l];
+        bs[q] = s;
+    }
+    __syncthreads();
+    if (grid_finish(bs, 3 * NK, D.part, cnt + b, blk, nblk, red)) {
+        for (int k = threadIdx.x; k < NK; k += blockDim.x) {
             const double s = C->scale[k0 + k];
-            C->h[k0 + k] = make_double2(s * red[2 * k], s * red[2 * k + 1]);
+            const double t1 = red[3 * k], t2 = red[3 * k + 1], t3 = red[3 * k + 2];
+            C->h[k0 + k] = three ? make_double2(s * (t1 + t2), s * (t3 + t1 - t2)) : make_double2(s * t1, s * t2);
         }
     }
 }
 
-// The accumulators of k_reorth_dots are compile-time sized.  A kernel built
-// for more vectors than a launch needs would still issue the FP64 multiply-adds
-// of the unused slots (predicated off, but occupying the FP64 pipe, which
-// bounds this kernel), so every count up to 24 has its own instantiation;
-// 25..28 and 29..32 share one.
+// The accumulators of k_reorth_dots are compile-time sized and a kernel
+// built for more vectors than a launch needs would still issue the FP64
+// multiply-adds of the unused slots, so every count up to kChunk has its own
+// instantiation (nk == NK in every launch).
 using DotsKernel = void (*)(const ColDesc*, const int4*, ColScalars*, int, int, int, int, unsigned*);
 
 template <int... N>
@@ -242,9 +318,8 @@ static constexpr std::array<DotsKernel, sizeof...(N)> dots_table(std::integer_se
 }
 
 static DotsKernel dots_kernel(int nk) {
-    static const std::array<DotsKernel, 24> exact = dots_table(std::make_integer_sequence<int, 24>{});
-    if (nk <= 24) return exact[nk - 1];
-    return nk <= 28 ? &k_reorth_dots<28> : &k_reorth_dots<32>;
+    static const std::array<DotsKernel, kChunk> exact = dots_table(std::make_integer_sequence<int, kChunk>{});
+    return exact[nk - 1];
 }
 
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
@@ -299,6 +374,9 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
     const double2* vj = Vb + (size_t)j * d;
     double2* out = Vb + (size_t)(j + 1) * d;
+    const float2* V32 = D.V32;
+    double* S1 = D.S ? D.S + (size_t)(j + 1) * d : nullptr;
+    float2* V32_1 = D.V32 ? D.V32 + (size_t)(j + 1) * d : nullptr;
     double acc[1] = {0.0};
     int em = 0;
     KG_FOR(i) {
@@ -310,13 +388,20 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         }
         float cx = 0.f, cy = 0.f;
         for (int k = 0; k < nk; ++k) {
-            const double2 v = Vb[(size_t)k * d + i];
             if (small[k]) {
+                // the FP32 plane when present (half the bytes), else truncate
+                float2 v32;
+                if (V32) {
+                    v32 = V32[(size_t)k * d + i];
+                } else {
+                    const double2 v = Vb[(size_t)k * d + i];
+                    v32 = make_float2(f64_to_f32_trunc(v.x), f64_to_f32_trunc(v.y));
+                }
                 const float2 c = coef32[k];
-                const float vx = f64_to_f32_trunc(v.x), vy = f64_to_f32_trunc(v.y);
-                cx = fmaf(c.x, vx, fmaf(-c.y, vy, cx));
-                cy = fmaf(c.x, vy, fmaf(c.y, vx, cy));
+                cx = fmaf(c.x, v32.x, fmaf(-c.y, v32.y, cx));
+                cy = fmaf(c.x, v32.y, fmaf(c.y, v32.x, cy));
             } else {
+                const double2 v = Vb[(size_t)k * d + i];
                 const double2 c = coef[k];
                 u.x -= fma(c.x, v.x, -c.y * v.y);
                 u.y -= fma(c.x, v.y, c.y * v.x);
@@ -325,6 +410,10 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         u.x -= (double)cx;
         u.y -= (double)cy;
         out[i] = u;
+        if (S1) {
+            S1[i] = u.x + u.y;
+            V32_1[i] = make_float2(f64_to_f32_trunc(u.x), f64_to_f32_trunc(u.y));
+        }
         acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
         em = max(em, max(exp_field(u.x), exp_field(u.y)));
     }
