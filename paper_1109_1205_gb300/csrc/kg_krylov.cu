@@ -350,9 +350,11 @@ constexpr double kSmallCoef = 1e-10;
 
 __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const int4* items, ColScalars* cs, int j,
                                                      int reorth, int second, unsigned* cnt) {
-    __shared__ double2 coef[kMaxMgs + 1];
+    // block-uniform term lists: FP32 terms (small coefficients), FP64 terms
+    __shared__ double2 coef64[kMaxMgs + 1];
     __shared__ float2 coef32[kMaxMgs + 1];
-    __shared__ int small[kMaxMgs + 1];
+    __shared__ int idx32[kMaxMgs + 1], idx64[kMaxMgs + 1];
+    __shared__ int n32, n64;
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
@@ -361,15 +363,25 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     const int d = D.d;
     double2* Vb = D.V;
     const int nk = reorth ? j + 1 : 0;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        const double s = C->scale[k];
-        const double2 h = C->h[k];
-        const double2 c = make_double2(s * h.x, s * h.y);
-        coef[k] = c;
-        coef32[k] = make_float2((float)c.x, (float)c.y);
-        small[k] = (fabs(h.x) + fabs(h.y)) < kSmallCoef;  // |h_k| for the unit vector v_k
+    if (threadIdx.x == 0) {
+        int a32 = 0, a64 = 0;
+        for (int k = 0; k < nk; ++k) {
+            const double s = C->scale[k];
+            const double2 h = C->h[k];
+            const double2 c = make_double2(s * h.x, s * h.y);
+            if ((fabs(h.x) + fabs(h.y)) < kSmallCoef) {  // |h_k| for the unit vector v_k
+                coef32[a32] = make_float2((float)c.x, (float)c.y);
+                idx32[a32++] = k;
+            } else {
+                coef64[a64] = c;
+                idx64[a64++] = k;
+            }
+        }
+        n32 = a32;
+        n64 = a64;
     }
     __syncthreads();
+    const int m32 = n32, m64 = n64;
     const double aj = C->alpha[j] * C->scale[j];
     const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
     const double2* vj = Vb + (size_t)j * d;
@@ -387,25 +399,38 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
             u.y = fma(-aj, p.y, u.y);
         }
         float cx = 0.f, cy = 0.f;
-        for (int k = 0; k < nk; ++k) {
-            if (small[k]) {
-                // the FP32 plane when present (half the bytes), else truncate
-                float2 v32;
-                if (V32) {
-                    v32 = V32[(size_t)k * d + i];
-                } else {
-                    const double2 v = Vb[(size_t)k * d + i];
-                    v32 = make_float2(f64_to_f32_trunc(v.x), f64_to_f32_trunc(v.y));
+        int q = 0;
+        if (V32) {
+            // four loads in flight before their terms are applied
+            for (; q + 4 <= m32; q += 4) {
+                float2 v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = V32[(size_t)idx32[q + r] * d + i];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 c = coef32[q + r];
+                    cx = fmaf(c.x, v[r].x, fmaf(-c.y, v[r].y, cx));
+                    cy = fmaf(c.x, v[r].y, fmaf(c.y, v[r].x, cy));
                 }
-                const float2 c = coef32[k];
-                cx = fmaf(c.x, v32.x, fmaf(-c.y, v32.y, cx));
-                cy = fmaf(c.x, v32.y, fmaf(c.y, v32.x, cy));
-            } else {
-                const double2 v = Vb[(size_t)k * d + i];
-                const double2 c = coef[k];
-                u.x -= fma(c.x, v.x, -c.y * v.y);
-                u.y -= fma(c.x, v.y, c.y * v.x);
             }
+            for (; q < m32; ++q) {
+                const float2 v = V32[(size_t)idx32[q] * d + i], c = coef32[q];
+                cx = fmaf(c.x, v.x, fmaf(-c.y, v.y, cx));
+                cy = fmaf(c.x, v.y, fmaf(c.y, v.x, cy));
+            }
+        } else {
+            for (; q < m32; ++q) {
+                const double2 v = Vb[(size_t)idx32[q] * d + i];
+                const float2 c = coef32[q];
+                const float vx = f64_to_f32_trunc(v.x), vy = f64_to_f32_trunc(v.y);
+                cx = fmaf(c.x, vx, fmaf(-c.y, vy, cx));
+                cy = fmaf(c.x, vy, fmaf(c.y, vx, cy));
+            }
+        }
+        for (int r = 0; r < m64; ++r) {
+            const double2 v = Vb[(size_t)idx64[r] * d + i], c = coef64[r];
+            u.x -= fma(c.x, v.x, -c.y * v.y);
+            u.y -= fma(c.x, v.y, c.y * v.x);
         }
         u.x -= (double)cx;
         u.y -= (double)cy;
@@ -414,7 +439,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
             S1[i] = u.x + u.y;
             V32_1[i] = make_float2(f64_to_f32_trunc(u.x), f64_to_f32_trunc(u.y));
         }
-        acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
+    acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
         em = max(em, max(exp_field(u.x), exp_field(u.y)));
     }
     em = block_max_int(em, smi);
