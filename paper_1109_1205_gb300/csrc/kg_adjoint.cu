@@ -311,11 +311,11 @@ static int build_space(Krylov& K, int reorth, cudaStream_t st) {
         if (reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));
-        KG_TRY(launch_update(K, j, reorth >= 1, false, st));
+        KG_TRY(launch_update(K, j, reorth, false, st));
         if (reorth >= 2) {
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), true, st));
-            KG_TRY(launch_update(K, j, 1, true, st));
+            KG_TRY(launch_update(K, j, reorth, true, st));
         }
     }
     return KG_OK;

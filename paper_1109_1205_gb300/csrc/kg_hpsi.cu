@@ -30,19 +30,6 @@ __device__ __forceinline__ double flip(double v, uint32_t code) {
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(code >> 31) << 63));
 }
 
-// Fixed-point image of x with the vector's largest exponent field E and
-// pre-shift P; the hop sign `neg` (0/1) is applied together with x's own.
-__device__ __forceinline__ long long fix_term(double x, int E, int P, uint32_t neg) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ffull);
-    const unsigned long long m = ((b & 0xfffffffffffffull) | 0x10000000000000ull) << P;
-    const int r = min(E - e, 63);
-    const unsigned long long half = (1ull << r) >> 1;
-    long long v = (long long)((m + half) >> r);
-    v = e ? v : 0ll;
-    return ((uint32_t)(b >> 63) ^ neg) ? -v : v;
-}
-
 template <int MODE>
 __device__ __forceinline__ void hop_acc(double2& acc, uint32_t code, double2 xs, const double2* amp) {
     if (MODE == 0) {
@@ -107,16 +94,86 @@ __device__ __forceinline__ void hop_sum(const SecView& S, const double2* __restr
     }
 }
 
-// 2^(E - 1075 - P): value of one unit of the fixed-point sums.
-__device__ __forceinline__ double fix_unit(int E, int P) {
-    const long long ex = (long long)E - 52 - P;  // biased exponent of the unit
-    return ex > 0 ? __longlong_as_double(ex << 52) : 0.0;
+// Conditional negation without a branch: m is 0 or -1.
+__device__ __forceinline__ long long neg_if(long long v, long long m) { return (v ^ m) - m; }
+
+// Hop part of (H x)[i_dn, i_up] from the fixed-point image Xf of x (all
+// components on one exponent, written by the kernel that produced x): the
+// same signed sums as the on-the-fly path, without the conversions.
+__device__ __forceinline__ void hop_sum_pre(const SecView& S, const longlong2* __restrict__ Xf, int i_dn, int i_up,
+                                            long long& ix, long long& iy) {
+    const int u0 = __ldg(S.up_off + i_up), u1 = __ldg(S.up_off + i_up + 1);
+    const int d0 = __ldg(S.dn_off + i_dn), d1 = __ldg(S.dn_off + i_dn + 1);
+    const longlong2* row = Xf + (size_t)i_dn * S.Du;
+#pragma unroll 4
+    for (int e = u0; e < u1; ++e) {
+        const uint2 en = __ldg(S.up_ent + e);
+        const longlong2 v = row[en.x];
+        const long long m = -(long long)(en.y >> 31);
+        ix += neg_if(v.x, m);
+        iy += neg_if(v.y, m);
+    }
+#pragma unroll 4
+    for (int e = d0; e < d1; ++e) {
+        const uint2 en = __ldg(S.dn_ent + e);
+        const longlong2 v = Xf[(size_t)en.x * S.Du + i_up];
+        const long long m = -(long long)(en.y >> 31);
+        ix += neg_if(v.x, m);
+        iy += neg_if(v.y, m);
+    }
 }
 
-__device__ __forceinline__ void stage_tables(const SecView& S, double2* amp, double* utab) {
+// v * 2^(E - 1075 - P) rounded to nearest (ties to even), assembled on the
+// integer pipe: the FP64 pipe of this GPU is the scarce one.  |v| < 2^62.
+// Falls back to FP64 arithmetic if the result would be subnormal.
+__device__ __forceinline__ double fix_to_double(long long v, int E, int P) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+    unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    const int n = 63 - __clzll((long long)a);  // position of the leading bit
+    int be = n + E - 52 - P;                    // biased exponent of the result
+    unsigned long long m;
+    if (n > 52) {
+        const int s = n - 52;
+        m = a >> s;
+        const unsigned long long rem = a & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++be;
+        }
+    } else {
+        m = a << (52 - n);
+    }
+    if (be < 1) {
+        const long long ex = (long long)E - 52 - P;
+        return ex > 0 ? __ll2double_rn(v) * __longlong_as_double(ex << 52) : 0.0;
+    }
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xfffffffffffffull)));
+}
+
+
+__device__ __forceinline__ void stage_amplitudes(const SecView& S, double2* amp) {
     for (int k = threadIdx.x; k < S.L * S.L; k += blockDim.x) amp[k] = S.hamp[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_diag_table(SecView S, double* diag) {
+    __shared__ double utab[4 * 256];
     for (int k = threadIdx.x; k < S.nchunk * 256; k += blockDim.x) utab[k] = S.Utab[k];
     __syncthreads();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.d; idx += gridDim.x * blockDim.x) {
+        int i_dn, i_up;
+        split_index(S, idx, i_dn, i_up);
+        diag[idx] = diag_energy(S, i_dn, i_up, utab);
+    }
+}
+
+int launch_diag_table(const SecView& S, double* diag, cudaStream_t st) {
+    const int nb = std::max(1, std::min((S.d + kThreads - 1) / kThreads, 148 * 16));
+    k_diag_table<<<nb, kThreads, 0, st>>>(S, diag);
+    KG_LAUNCHED();
+    return KG_OK;
 }
 
 // Largest exponent field over the components of x, into *emax (pre-set to 0).
@@ -135,22 +192,20 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_hpsi(SecView S, const double2* __restrict__ x,
                                                    double2* __restrict__ y, const int* emax) {
     __shared__ double2 amp[kMaxL * kMaxL];
-    __shared__ double utab[4 * 256];
-    stage_tables(S, amp, utab);
+    stage_amplitudes(S, amp);
     const int E = (MODE == 3) ? *emax : 0;
-    const double unit = (MODE == 3) ? fix_unit(E, S.fix_pre) * S.h0 : 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.d; idx += gridDim.x * blockDim.x) {
         int i_dn, i_up;
         split_index(S, idx, i_dn, i_up);
         const double2 xv = x[idx];
-        const double diag = diag_energy(S, i_dn, i_up, utab);
+        const double diag = __ldg(S.diag + idx);
         double2 hop = make_double2(0.0, 0.0);
         long long ix = 0, iy = 0;
         hop_sum<MODE>(S, x, i_dn, i_up, amp, E, hop, ix, iy);
         double2 r;
         if (MODE == 3) {
-            r.x = fma(diag, xv.x, unit * __ll2double_rn(ix));
-            r.y = fma(diag, xv.y, unit * __ll2double_rn(iy));
+            r.x = fma(diag, xv.x, S.h0 * fix_to_double(ix, E, S.fix_pre));
+            r.y = fma(diag, xv.y, S.h0 * fix_to_double(iy, E, S.fix_pre));
         } else if (MODE == 0) {
             r.x = fma(diag, xv.x, S.h0 * hop.x);
             r.y = fma(diag, xv.y, S.h0 * hop.y);
@@ -165,42 +220,60 @@ __global__ void __launch_bounds__(kThreads) k_hpsi(SecView S, const double2* __r
 // Lanczos step j for column b of a work-list launch:
 //   w = s_j H V_j - b_j s_{j-1} V_{j-1},   a_j = Re <s_j V_j, w>
 // (Eq. (recursion) with normalised v_k = s_k V_k).
+struct HpsiShared {
+    double2 amp[kMaxL * kMaxL];
+    double sm[(kThreads / 32) * 2];
+    int smi[kThreads / 32];
+    double bs[2], red[2];
+    SecView S;
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, const int4* items, ColScalars* cs,
-                                                           int j, unsigned* cnt) {
-    __shared__ double2 amp[kMaxL * kMaxL];
-    __shared__ double utab[4 * 256];
-    __shared__ double sm[(kThreads / 32) * 2];
-    __shared__ double bs[2], red[2];
-    __shared__ SecView S;
-    KG_ITEM();
+__device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalars* cs, int j, unsigned* cnt,
+                                                  const int4 it_, HpsiShared& sh) {
+    const int b = it_.x, blk = it_.y, nblk = it_.z;
+    const ColDesc D = desc[b];
+    ColScalars* C = cs + b;
+    SecView& S = sh.S;
+    double2* amp = sh.amp;
+    double *sm = sh.sm, *bs = sh.bs, *red = sh.red;
+    int* smi = sh.smi;
     if (j >= C->m_eff) return;
+    __syncthreads();  // the previous item (round lists) is done with S and amp
     if (threadIdx.x == 0) S = *D.sec;
     __syncthreads();
-    stage_tables(S, amp, utab);
+    stage_amplitudes(S, amp);
     const double sj = C->scale[j];
     const double cprev = (j > 0) ? C->beta[j] * C->scale[j - 1] : 0.0;
     const int E = (MODE == 3) ? C->emax[j] : 0;
-    const double unit = (MODE == 3) ? fix_unit(E, S.fix_pre) * S.h0 * sj : 0.0;
     const double hs = S.h0 * sj;
+    // V_j in fixed point, written by the update that produced it (not V_0),
+    // used when its exponent bound is tight enough
+    const int Ef = C->efix;
+    const bool pre = MODE == 3 && j > 0 && D.Xf != nullptr && Ef >= E && Ef - E <= kFixSlack;
     const double2* x = D.V + (size_t)j * D.d;
     const double2* xp = D.V + (size_t)(j > 0 ? j - 1 : 0) * D.d;
     double2* w = D.W;
     double acc[2] = {0.0, 0.0};
+    int ew = 0;
     KG_FOR(idx) {
         int i_dn, i_up;
         split_index(S, idx, i_dn, i_up);
         const double2 xv = x[idx];
-        const double sdiag = sj * diag_energy(S, i_dn, i_up, utab);
+        const double sdiag = sj * __ldg(S.diag + idx);
         double2 hop = make_double2(0.0, 0.0);
         long long ix = 0, iy = 0;
-        hop_sum<MODE>(S, x, i_dn, i_up, amp, E, hop, ix, iy);
+        const int Eu = pre ? Ef : E;
+        if (MODE == 3 && pre)
+            hop_sum_pre(S, D.Xf, i_dn, i_up, ix, iy);
+        else
+            hop_sum<MODE>(S, x, i_dn, i_up, amp, E, hop, ix, iy);
         double2 p = make_double2(0.0, 0.0);
         if (j > 0) p = xp[idx];
         double2 r;
         if (MODE == 3) {
-            r.x = fma(sdiag, xv.x, fma(unit, __ll2double_rn(ix), -cprev * p.x));
-            r.y = fma(sdiag, xv.y, fma(unit, __ll2double_rn(iy), -cprev * p.y));
+            r.x = fma(sdiag, xv.x, fma(hs, fix_to_double(ix, Eu, S.fix_pre), -cprev * p.x));
+            r.y = fma(sdiag, xv.y, fma(hs, fix_to_double(iy, Eu, S.fix_pre), -cprev * p.y));
         } else if (MODE == 0) {
             r.x = fma(sdiag, xv.x, fma(hs, hop.x, -cprev * p.x));
             r.y = fma(sdiag, xv.y, fma(hs, hop.y, -cprev * p.y));
@@ -210,19 +283,32 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, 
         }
         w[idx] = r;
         acc[0] = fma(xv.x, r.x, fma(xv.y, r.y, acc[0]));  // Re conj(x) r
+        ew = max(ew, max(exp_field(r.x), exp_field(r.y)));
     }
     acc[0] *= sj;
+    ew = block_max_int(ew, smi);
     block_sum<2>(acc, 1, sm, bs);
-    if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red)) {
+    if (threadIdx.x == 0) bs[1] = (double)ew;
+    __syncthreads();
+    if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red, 1)) {
         if (threadIdx.x == 0) {
             const double a = red[0];
             C->alpha[j] = a;
+            C->ew = (int)red[1];
             if (!isfinite(a)) {
                 C->status = KG_ENUMERIC;
                 C->m_eff = j + 1;
             }
         }
     }
+}
+
+// One item per block (one-wave work lists, batches of any mix of sizes).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                           int j, unsigned* cnt) {
+    __shared__ HpsiShared sh;
+    lanczos_hpsi_item<MODE>(desc, cs, j, cnt, items[blockIdx.x], sh);
 }
 
 int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st) {
@@ -262,7 +348,7 @@ int prepare_hpsi_lists(Krylov& K) {
         if (!present[mode]) continue;
         const int4* items;
         int n;
-        KG_TRY(work_list(K, kerns[mode], mode, &items, &n));
+        for (int g = 0; g < K.ngroups[mode]; ++g) KG_TRY(work_list(K, kerns[mode], mode, &items, &n, g));
     }
     return KG_OK;
 }
@@ -279,14 +365,17 @@ int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st) {
                                        : (const void*)k_lanczos_hpsi<2>;
         const int4* items;
         int n;
-        KG_TRY(work_list(K, kern, mode, &items, &n));
-        switch (mode) {
-            case 3: k_lanczos_hpsi<3><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-            case 0: k_lanczos_hpsi<0><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-            case 1: k_lanczos_hpsi<1><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-            default: k_lanczos_hpsi<2><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+        // one launch per group of columns whose gathered vectors fit in L2
+        for (int g = 0; g < K.ngroups[mode]; ++g) {
+            KG_TRY(work_list(K, kern, mode, &items, &n, g));
+            switch (mode) {
+                case 3: k_lanczos_hpsi<3><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+                case 0: k_lanczos_hpsi<0><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+                case 1: k_lanczos_hpsi<1><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+                default: k_lanczos_hpsi<2><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+            }
+            KG_LAUNCHED();
         }
-        KG_LAUNCHED();
     }
     return KG_OK;
 }

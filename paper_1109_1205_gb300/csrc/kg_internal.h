@@ -21,6 +21,9 @@ constexpr int kChunk = 24;     // complex dot products accumulated per pass
 constexpr int kMaxOv = 32;     // overlap vectors fused into the combination pass
 constexpr int kPart = 72;      // doubles per block in a partial-sum row
 constexpr int kThreads = 256;  // threads per block of the streaming kernels
+// H*psi gathers each input component about once per hop; a launch covers a
+// group of columns whose inputs together fit in this much L2 (of 129 MB).
+constexpr long long kHpsiGroupBytes = 72ll << 20;
 
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
@@ -74,6 +77,7 @@ struct SecView {
     const double* dn_e;
     const double2* hamp;  // [L*L] hopping amplitudes h_ab
     const double* Utab;   // [nchunk * 256] U summed over the set bits of a byte
+    const double* diag;   // [d] diagonal of H (eps, h_ii and U terms) per state
     int nchunk;
     int hopmode;          // 0: all hops share the real amplitude h0; 1: real; 2: complex
     double h0;
@@ -94,6 +98,7 @@ struct kg_sector {
     kg::SpinTables up, dn;
     double2* hamp = nullptr;
     double* Utab = nullptr;
+    double* diag = nullptr;  // [d] diagonal of H
     int nchunk = 1;
     kg_sector* nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][dagger]
     bool is_child = false;
@@ -126,6 +131,8 @@ struct ColScalars {
     int m_eff;                  // Krylov dimension reached (smaller after a breakdown)
     int status;                 // KG_OK, KG_ENUMERIC or KG_ENOCONV
     int ov_slot;                // overlap rows written so far
+    int ew;                     // largest exponent field of the last H*psi output W
+    int efix;                   // exponent of the fixed-point image Xf of the newest V_k
     int pad;
 };
 
@@ -137,6 +144,7 @@ struct ColDesc {
     double2* V;             // [M+1][d] Lanczos vectors (unnormalised)
     double* S;              // [M+1][d] Re + Im of each component of V_k (or null)
     float2* V32;            // [M+1][d] V_k truncated to FP32 (or null)
+    longlong2* Xf;          // [d] fixed-point image of the next H*psi input (or null)
     double2* W;             // [d] H v workspace
     double* part;           // [nblk_max][kPart] partial sums of this column
     double2* out;           // where the combination writes (V_0 by default)
@@ -146,6 +154,7 @@ struct ColDesc {
     double tau;             // propagation step of this column
     int d, n_ov, ov_rows, nblk_max;
     int mode;               // hop sums: 0 FP64 uniform, 1 real, 2 complex, 3 exact integer
+    int Du, Dd, fix_pre;    // row length, row count, fixed-point pre-shift of the sector
     int pad;
 };
 
@@ -167,9 +176,12 @@ struct Krylov {
     double2* Vbuf = nullptr;
     double* Sbuf = nullptr;         // planes of the Gram-Schmidt kernels (optional)
     float2* V32buf = nullptr;
+    longlong2* Xfbuf = nullptr;     // fixed-point H*psi inputs of exact-integer columns
     double2* Wbuf = nullptr;
     double* partbuf = nullptr;
     std::map<long long, std::pair<int4*, int>> lists;
+    std::vector<int> group;         // H*psi launch group of each column (per mode)
+    int ngroups[4] = {0, 0, 0, 0};  // groups per hop-sum mode
     double2* vec(int b, int k) const { return hdesc[b].V + (size_t)k * hdesc[b].d; }
     int dim(int b) const { return hdesc[b].d; }
 };
@@ -179,7 +191,7 @@ struct Krylov {
 int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, bool int_hops);
 int krylov_upload(Krylov& K, cudaStream_t st);  // after editing hdesc (tau, out, overlaps)
 void krylov_free(Krylov& K);
-int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n);
+int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n, int group = -1);
 
 // ----------------------------------------------------------- launchers
 // y = H x (plain).
@@ -194,7 +206,10 @@ int launch_colnorm(Krylov& K, cudaStream_t st);
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st);
 // Lanczos update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
 // second pass), then b_{j+1} = ||V_{j+1}||, scale, breakdown test.
-int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st);
+// level: the reorthogonalisation level (0, 1, 2); second: the second pass.
+// diag[s] = e_up[i_up] + e_dn[i_dn] + sum of U over doubly occupied sites.
+int launch_diag_table(const SecView& S, double* diag, cudaStream_t st);
+int launch_update(Krylov& K, int j, int level, bool second, cudaStream_t st);
 // Tridiagonal step: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1
 // with each column's tau; mode 1: ground-state Ritz pair (lam0, c = q_0).
 int launch_tridiag(Krylov& K, int mode, cudaStream_t st);
@@ -365,6 +380,27 @@ __device__ __forceinline__ int block_max_int(int v, int* sm) {
 __device__ __forceinline__ int exp_field(double x) {
     return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu);
 }
+
+// Fixed-point image round(x * 2^(1075 + P - E)) of x, for E at least the
+// exponent field of x (so |result| < 2^(53 + P)); `neg` (0/1) flips the sign
+// together with x's own.  Exponent field 0 (zero, subnormal) gives 0.
+__device__ __forceinline__ long long fix_term(double x, int E, int P, uint32_t neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = ((b & 0xfffffffffffffull) | 0x10000000000000ull) << P;
+    const int r = min(E - e, 63);
+    const unsigned long long half = (1ull << r) >> 1;
+    long long v = (long long)((m + half) >> r);
+    v = e ? v : 0ll;
+    return ((uint32_t)(b >> 63) ^ neg) ? -v : v;
+}
+
+// The fixed-point image of V_{j+1} is written by the update with an exponent
+// bound known before the vector exists; H*psi uses it when the bound exceeds
+// the vector's true largest exponent by at most kFixSlack bits (each bit
+// costs one bit of the fixed-point sums' precision, which has P >= 4 bits to
+// spare over FP64), and converts on the fly otherwise.
+constexpr int kFixSlack = 4;
 
 // Deterministic reduction over the nblk blocks of one column (block `row`).
 // Each block stores its nv + nmax totals (bsum, in shared memory) into its

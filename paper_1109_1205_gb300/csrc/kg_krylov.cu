@@ -34,7 +34,7 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         set_error("empty Krylov batch");
         return KG_EINVAL;
     }
-    size_t nv = 0, nw = 0, np = 0;
+    size_t nv = 0, nw = 0, np = 0, nx = 0;
     for (auto* s : cols) K.total_d += s->d;
     K.hdesc.resize(K.B);
     K.hsec.resize(K.B);
@@ -43,15 +43,55 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         ColDesc& D = K.hdesc[b];
         std::memset(&D, 0, sizeof D);
         D.d = (int)s->d;
-        // partial-sum rows: enough for a one-wave list (<= 8 blocks per SM)
-        // of any kernel at up to twice the wave, shared in proportion to d
-        const long long want = (long long)std::ceil(16.0 * nsm * (double)s->d / (double)K.total_d) + 2;
-        D.nblk_max = (int)std::max(1LL, std::min(want, (long long)(s->d + kThreads - 1) / kThreads));
         K.hsec[b] = s->view();
         const SecView& S = K.hsec[b];
         D.mode = S.hopmode == 0 ? ((int_hops && S.fix_pre >= 0) ? 3 : 0) : S.hopmode;
+        D.Du = S.Du;
+        D.Dd = S.Dd;
+        D.fix_pre = S.fix_pre;
+        if (D.mode == 3) nx += (size_t)D.d;
         nv += (size_t)(M + 1) * D.d;
         nw += (size_t)D.d;
+    }
+    // H*psi groups: consecutive columns of one mode while their inputs fit
+    // kHpsiGroupBytes; then partial-sum rows for a one-wave list (<= 8 blocks
+    // per SM) of any kernel at up to twice the wave, shared in proportion to
+    // d over the batch or over the column's group, whichever is larger
+    K.group.assign(K.B, 0);
+    std::vector<long long> gbytes, gd;
+    {
+        // balanced: as few groups as the budget allows, filled to the mean
+        long long mbytes[4] = {0, 0, 0, 0};
+        for (auto& D : K.hdesc) mbytes[D.mode] += 16LL * D.d;
+        long long target[4];
+        for (int m = 0; m < 4; ++m) {
+            const long long ng = std::max(1LL, (mbytes[m] + kHpsiGroupBytes - 1) / kHpsiGroupBytes);
+            target[m] = (mbytes[m] + ng - 1) / ng;
+        }
+        int cur[4] = {-1, -1, -1, -1};
+        for (int b = 0; b < K.B; ++b) {
+            ColDesc& D = K.hdesc[b];
+            const long long bytes = 16LL * D.d;
+            if (cur[D.mode] < 0 || gbytes[cur[D.mode]] + bytes > target[D.mode]) {
+                cur[D.mode] = (int)gbytes.size();
+                gbytes.push_back(0);
+                gd.push_back(0);
+                K.group[b] = K.ngroups[D.mode]++;
+            } else {
+                K.group[b] = K.ngroups[D.mode] - 1;
+            }
+            gbytes[cur[D.mode]] += bytes;
+            gd[cur[D.mode]] += D.d;
+            D.pad = cur[D.mode];  // global group slot, used below only
+        }
+    }
+    np = 0;
+    for (int b = 0; b < K.B; ++b) {
+        ColDesc& D = K.hdesc[b];
+        const double share = std::max((double)D.d / (double)K.total_d, (double)D.d / (double)gd[D.pad]);
+        const long long want = (long long)std::ceil(16.0 * nsm * share) + 2;
+        D.nblk_max = (int)std::max(1LL, std::min(want, (long long)(D.d + kThreads - 1) / kThreads));
+        D.pad = 0;
         np += (size_t)D.nblk_max * kPart;
     }
     KG_CUDA(cudaMalloc(&K.Vbuf, sizeof(double2) * nv));
@@ -63,10 +103,12 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         cudaGetLastError();
         cudaFree(K.Sbuf);
         cudaFree(K.V32buf);
+    cudaFree(K.Xfbuf);
         K.Sbuf = nullptr;
         K.V32buf = nullptr;
     }
     KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * nw));
+    if (nx) KG_CUDA(cudaMalloc(&K.Xfbuf, sizeof(longlong2) * nx));
     KG_CUDA(cudaMalloc(&K.partbuf, sizeof(double) * np));
     KG_CUDA(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B));
     KG_CUDA(cudaMalloc(&K.secs, sizeof(SecView) * K.B));
@@ -75,13 +117,17 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
     KG_CUDA(cudaMalloc(&K.Q, sizeof(double) * (size_t)K.B * M * M));
     KG_CUDA(cudaMemset(K.cs, 0, sizeof(ColScalars) * K.B));
     KG_CUDA(cudaMemset(K.cnt, 0, sizeof(unsigned) * K.B));
-    size_t ov = 0, ow = 0, op = 0;
+    size_t ov = 0, ow = 0, op = 0, ox = 0;
     for (int b = 0; b < K.B; ++b) {
         ColDesc& D = K.hdesc[b];
         D.sec = K.secs + b;
         D.V = K.Vbuf + ov;
         D.S = K.Sbuf ? K.Sbuf + ov : nullptr;
         D.V32 = K.V32buf ? K.V32buf + ov : nullptr;
+        if (D.mode == 3) {
+            D.Xf = K.Xfbuf + ox;
+            ox += (size_t)D.d;
+        }
         D.W = K.Wbuf + ow;
         D.part = K.partbuf + op;
         D.out = D.V;
@@ -104,6 +150,7 @@ void krylov_free(Krylov& K) {
     cudaFree(K.Vbuf);
     cudaFree(K.Sbuf);
     cudaFree(K.V32buf);
+    cudaFree(K.Xfbuf);
     cudaFree(K.Wbuf);
     cudaFree(K.partbuf);
     cudaFree(K.desc);
@@ -126,21 +173,26 @@ static int occupancy(const void* kern) {
     return bps;
 }
 
-// Work list of a kernel over the columns whose mode is `mode` (-1: all):
-// column b gets blocks in proportion to its dimension, one wave in total.
-int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n) {
+// Work list of a kernel over the columns whose mode is `mode` (-1: all) and,
+// with group >= 0, whose H*psi group is `group`: column b gets blocks in
+// proportion to its dimension, one wave in total.
+int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n, int group) {
     const int bps = occupancy(kern);
-    const long long key = ((long long)bps << 8) + (mode + 1) + ((long long)std::lround(K.wave_scale * 64.0) << 20);
+    const long long key = ((long long)bps << 8) + (mode + 1) + ((long long)std::lround(K.wave_scale * 64.0) << 20) +
+                          ((long long)(group + 1) << 32);
     auto it = K.lists.find(key);
     if (it == K.lists.end()) {
+        auto take = [&](const ColDesc& D, int b) {
+            return (mode < 0 || D.mode == mode) && (group < 0 || K.group[b] == group);
+        };
         long long dsel = 0;
-        for (auto& D : K.hdesc)
-            if (mode < 0 || D.mode == mode) dsel += D.d;
+        for (int b = 0; b < K.B; ++b)
+            if (take(K.hdesc[b], b)) dsel += K.hdesc[b].d;
         const double total = std::max(1.0, K.wave_scale * K.nsm * bps);
         std::vector<int4> v;
         for (int b = 0; b < K.B; ++b) {
             const ColDesc& D = K.hdesc[b];
-            if (mode >= 0 && D.mode != mode) continue;
+            if (!take(D, b)) continue;
             int nb = (int)std::lround(total * (double)D.d / (double)std::max(1LL, dsel));
             nb = std::max(1, std::min(nb, std::min(D.nblk_max, (D.d + kThreads - 1) / kThreads)));
             for (int k = 0; k < nb; ++k) v.push_back(make_int4(b, k, nb, 0));
@@ -349,12 +401,12 @@ int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream
 constexpr double kSmallCoef = 1e-10;
 
 __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const int4* items, ColScalars* cs, int j,
-                                                     int reorth, int second, unsigned* cnt) {
+                                                     int level, int second, unsigned* cnt) {
     // block-uniform term lists: FP32 terms (small coefficients), FP64 terms
     __shared__ double2 coef64[kMaxMgs + 1];
     __shared__ float2 coef32[kMaxMgs + 1];
     __shared__ int idx32[kMaxMgs + 1], idx64[kMaxMgs + 1];
-    __shared__ int n32, n64;
+    __shared__ int n32, n64, efix_s;
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
@@ -362,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     if (j >= C->m_eff) return;
     const int d = D.d;
     double2* Vb = D.V;
-    const int nk = reorth ? j + 1 : 0;
+    const int nk = (level >= 1 || second) ? j + 1 : 0;
     if (threadIdx.x == 0) {
         int a32 = 0, a64 = 0;
         for (int k = 0; k < nk; ++k) {
@@ -391,7 +443,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     float2* V32_1 = D.V32 ? D.V32 + (size_t)(j + 1) * d : nullptr;
     double acc[1] = {0.0};
     int em = 0;
-    KG_FOR(i) {
+    auto element = [&](int i) {
         double2 u = w[i];
         if (!second) {
             const double2 p = vj[i];
@@ -439,8 +491,41 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
             S1[i] = u.x + u.y;
             V32_1[i] = make_float2(f64_to_f32_trunc(u.x), f64_to_f32_trunc(u.y));
         }
-    acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
+        acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
         em = max(em, max(exp_field(u.x), exp_field(u.y)));
+        return u;
+    };
+    if (D.Xf && (second || level < 2)) {
+        // Last pass of an exact-integer column: also write the fixed-point
+        // image of V_{j+1} that the next H*psi reads, on the exponent efix.
+        // The vector's largest exponent is only known at the end of this
+        // kernel, so efix bounds it from the inputs: every component of the
+        // result is below
+        //   2^(E_u - 1022) + |a_j| 2^(E_j - 1022) + sum_k (|Re c_k| + |Im c_k|) 2^(E_k - 1022)
+        // (E_u: largest exponent of W, or of V_{j+1} in a second pass), times
+        // a margin for the rounding of the FP64 and FP32 arithmetic.
+        if (threadIdx.x == 0) {
+            const int Eu = second ? C->emax[j + 1] : C->ew;
+            double r = 1.0;
+            if (!second) r += fabs(aj) * ldexp(1.0, C->emax[j] - Eu);
+            for (int q = 0; q < m32; ++q)
+                r += (fabs((double)coef32[q].x) + fabs((double)coef32[q].y)) * ldexp(1.0, C->emax[idx32[q]] - Eu);
+            for (int q = 0; q < m64; ++q)
+                r += (fabs(coef64[q].x) + fabs(coef64[q].y)) * ldexp(1.0, C->emax[idx64[q]] - Eu);
+            r *= 1.0 + 1.0 / 1024.0;
+            int ex;
+            const double fr = frexp(r, &ex);  // r = fr * 2^ex, fr in [0.5, 1)
+            efix_s = Eu + (fr == 0.5 ? ex - 1 : ex);
+        }
+        __syncthreads();
+        const int Ef = efix_s, P = D.fix_pre;
+        KG_FOR(i) {
+            const double2 u = element(i);
+            D.Xf[i] = make_longlong2(fix_term(u.x, Ef, P, 0u), fix_term(u.y, Ef, P, 0u));
+        }
+        if (blk == 0 && threadIdx.x == 0) C->efix = Ef;
+    } else {
+        KG_FOR(i) element(i);
     }
     em = block_max_int(em, smi);
     block_sum<1>(acc, 1, sm, bs);
@@ -450,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         C->emax[j + 1] = (int)red[1];
         const double n = sqrt(red[0]);
         double a = C->alpha[j];
-        if (reorth) a += C->h[j].x;
+        if (nk) a += C->h[j].x;
         C->alpha[j] = a;
         C->beta[j + 1] = n;
         C->scale[j + 1] = n > 0.0 ? 1.0 / n : 0.0;
@@ -464,12 +549,12 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     }
 }
 
-int launch_update(Krylov& K, int j, int reorth, bool second, cudaStream_t st) {
+int launch_update(Krylov& K, int j, int level, bool second, cudaStream_t st) {
     ProfScope ps("update", st);
     const int4* items;
     int n;
     KG_TRY(work_list(K, (const void*)k_update, -1, &items, &n));
-    k_update<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, reorth ? 1 : 0, second ? 1 : 0, K.cnt);
+    k_update<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, level, second ? 1 : 0, K.cnt);
     KG_LAUNCHED();
     return KG_OK;
 }
@@ -788,11 +873,11 @@ int enqueue_step(Krylov& K, int reorth, cudaStream_t st) {
         if (reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));
-        KG_TRY(launch_update(K, j, reorth >= 1, false, st));
+        KG_TRY(launch_update(K, j, reorth, false, st));
         if (reorth >= 2) {
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), true, st));
-            KG_TRY(launch_update(K, j, 1, true, st));
+            KG_TRY(launch_update(K, j, reorth, true, st));
         }
     }
     KG_TRY(launch_tridiag(K, 0, st));
@@ -836,11 +921,11 @@ int ground_state(kg_sector* s, const kg_opts* o) {
             rc = launch_lanczos_hpsi(K, j, st);
             for (int k0 = 0; rc == KG_OK && k0 <= j; k0 += kChunk)
                 rc = launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st);
-            if (rc == KG_OK) rc = launch_update(K, j, 1, false, st);
+            if (rc == KG_OK) rc = launch_update(K, j, std::max(1, o->reorth), false, st);
             if (rc == KG_OK && o->reorth >= 2) {
                 for (int k0 = 0; rc == KG_OK && k0 <= j; k0 += kChunk)
                     rc = launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), true, st);
-                if (rc == KG_OK) rc = launch_update(K, j, 1, true, st);
+                if (rc == KG_OK) rc = launch_update(K, j, o->reorth, true, st);
             }
         }
         if (rc == KG_OK) rc = launch_tridiag(K, 1, st);

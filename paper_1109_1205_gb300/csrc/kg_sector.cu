@@ -311,6 +311,15 @@ int sector_build(int L, int nu, int nd, const double* h_re, const double* h_im, 
     }
     cudaMemcpy(s->hamp, hamp.data(), sizeof(double2) * L * L, cudaMemcpyHostToDevice);
     cudaMemcpy(s->Utab, utab.data(), sizeof(double) * utab.size(), cudaMemcpyHostToDevice);
+    if (cudaMalloc(&s->diag, sizeof(double) * s->d) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of the diagonal table failed (%lld states)", s->d);
+        return fail(KG_ENOMEM);
+    }
+    rc = launch_diag_table(s->view(), s->diag, s->stream);
+    if (rc == KG_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "diagonal table", __FILE__, __LINE__);
+    if (rc != KG_OK) return fail(rc);
     *out = s;
     return KG_OK;
 }
@@ -323,6 +332,7 @@ void sector_free(kg_sector* s) {
     free_spin(s->dn);
     cudaFree(s->hamp);
     cudaFree(s->Utab);
+    cudaFree(s->diag);
     cudaFree(s->gs);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->fence) cudaEventDestroy(s->fence);
@@ -453,6 +463,7 @@ kg::SecView kg_sector::view() const {
     v.dn_e = dn.e;
     v.hamp = hamp;
     v.Utab = Utab;
+    v.diag = diag;
     v.nchunk = nchunk;
     v.hopmode = hopmode;
     v.h0 = h0;
