@@ -570,7 +570,14 @@ int launch_update(Krylov& K, int j, int level, bool second, cudaStream_t st) {
 //       lam0, lam1 = two lowest Ritz values, resest = |b_m Q[m-1][m0]|.
 // The stored combination coefficient is c_k * s_k (Lanczos vectors are
 // unnormalised).
-constexpr int kTriWarps = 4;
+//
+// On this GPU a warp's FP64 instruction occupies the FP64 pipe for many
+// cycles even with one active lane, so the serial chase is what costs: each
+// rotation takes one reciprocal square root instead of a hypot and two
+// divisions, and Q stays in shared memory for m <= 32 (every propagation
+// step), so that applying a sweep's rotations does not wait on L2.
+constexpr int kTriWarps = 2;
+constexpr int kTriSmemQ = 32;
 
 __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc, ColScalars* cs, int B, int Mcap,
                                                            double* Qall, int mode, const double* taus, int ntau,
@@ -578,13 +585,14 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
     __shared__ double sd[kTriWarps][kMaxMgs], se[kTriWarps][kMaxMgs];
     __shared__ double rc[kTriWarps][kMaxMgs], rs[kTriWarps][kMaxMgs];
     __shared__ int ctl[kTriWarps][4];
+    __shared__ double sQ[kTriWarps][kTriSmemQ * kTriSmemQ];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * kTriWarps + warp;
     if (b >= B) return;
     ColScalars* C = cs + b;
     const double tau = desc[b].tau;
     const int m = C->m_eff;
-    double* Q = Qall + (size_t)b * Mcap * Mcap;
+    double* Q = m <= kTriSmemQ ? sQ[warp] : Qall + (size_t)b * Mcap * Mcap;
     double* d = sd[warp];
     double* e = se[warp];
     if (m == 0) {
@@ -624,11 +632,14 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
                 const double mu = d[hi] - bb * bb / den;
                 double x = d[lo] - mu, z = e[lo];
                 for (int k = lo; k < hi; ++k) {
-                    const double r = hypot(x, z);
-                    double c = 1.0, s = 0.0;
-                    if (r > 0.0) {
-                        c = x / r;
-                        s = z / r;
+                    // Givens rotation zeroing z against x: r = |(x, z)|
+                    const double r2 = fma(x, x, z * z);
+                    double c = 1.0, s = 0.0, r = 0.0;
+                    if (r2 > 0.0) {
+                        const double inv = rsqrt(r2);
+                        c = x * inv;
+                        s = z * inv;
+                        r = r2 * inv;
                     }
                     if (k > lo) e[k - 1] = r;
                     const double ak = d[k], ak1 = d[k + 1], bk = e[k];
@@ -728,16 +739,50 @@ int launch_tridiag(Krylov& K, int mode, cudaStream_t st) {
 // ||out|| and <ov_a, out> for the column's n_ov overlap vectors, written to
 // row cs[b].ov_slot of its overlap table (the slot advances by one).  NOV
 // bounds n_ov at compile time so that the accumulators stay in registers.
+//
+// The Krylov coefficients decay quickly with k.  As in the update, a term
+// whose coefficient on the unit vector v_k is below 1e-10 of the largest one
+// (which bounds ||out||) is summed in FP32 from the truncated plane; the
+// others use three FP64 multiply-adds per element with the Re+Im plane
+// (c = p + iq, v = a + ib: T1 = p a, T2 = q b, T3 = (p + q)(a + b),
+// Re = T1 - T2, Im = T3 - T1 - T2), or four without it.
 template <int NOV>
 __global__ void __launch_bounds__(kThreads) k_combine(const ColDesc* desc, const int4* items, ColScalars* cs,
                                                       unsigned* cnt) {
     __shared__ double2 coef[kMaxMgs];
+    __shared__ double csum[kMaxMgs];
+    __shared__ int idx64[kMaxMgs], idx32[kMaxMgs];
+    __shared__ float2 coef32[kMaxMgs];
+    __shared__ int n64, n32;
     __shared__ double sm[(kThreads / 32) * (2 * NOV + 2)];
     __shared__ double bs[2 * NOV + 2], red[2 * NOV + 2];
     KG_ITEM();
     const int m = C->m_eff;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) coef[k] = C->c[k];
+    if (threadIdx.x == 0) {
+        double cmax = 0.0;
+        for (int k = 0; k < m; ++k) {
+            const double2 c = C->c[k];
+            const double sk = C->scale[k];
+            if (sk > 0.0) cmax = fmax(cmax, (fabs(c.x) + fabs(c.y)) / sk);
+        }
+        int a64 = 0, a32 = 0;
+        for (int k = 0; k < m; ++k) {
+            const double2 c = C->c[k];
+            const double sk = C->scale[k];
+            if (D.V32 && sk > 0.0 && (fabs(c.x) + fabs(c.y)) < 1e-10 * cmax * sk) {
+                coef32[a32] = make_float2((float)c.x, (float)c.y);
+                idx32[a32++] = k;
+            } else {
+                coef[a64] = c;
+                csum[a64] = c.x + c.y;
+                idx64[a64++] = k;
+            }
+        }
+        n64 = a64;
+        n32 = a32;
+    }
     __syncthreads();
+    const int m64 = n64, m32 = n32;
     const int d = D.d;
     const int n_ov = D.n_ov;
     const double2* Vb = D.V;
@@ -745,13 +790,52 @@ __global__ void __launch_bounds__(kThreads) k_combine(const ColDesc* desc, const
     double acc[2 * NOV + 2];
 #pragma unroll
     for (int k = 0; k < 2 * NOV + 2; ++k) acc[k] = 0.0;
+    const double* Sb = D.S;
+    const float2* V32 = D.V32;
     KG_FOR(i) {
-        double2 u = make_double2(0.0, 0.0);
-        for (int k = 0; k < m; ++k) {
-            const double2 v = Vb[(size_t)k * d + i];
-            const double2 c = coef[k];
-            u.x = fma(c.x, v.x, fma(-c.y, v.y, u.x));
-            u.y = fma(c.x, v.y, fma(c.y, v.x, u.y));
+        double2 u;
+        if (Sb) {
+            double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int q = 0; q < m64; ++q) {
+                const size_t o_ = (size_t)idx64[q] * d + i;
+                const double2 v = Vb[o_];
+                const double sv = Sb[o_];
+                const double2 c = coef[q];
+                t1 = fma(c.x, v.x, t1);
+                t2 = fma(c.y, v.y, t2);
+                t3 = fma(csum[q], sv, t3);
+            }
+            u = make_double2(t1 - t2, t3 - t1 - t2);
+        } else {
+            u = make_double2(0.0, 0.0);
+            for (int q = 0; q < m64; ++q) {
+                const double2 v = Vb[(size_t)idx64[q] * d + i];
+                const double2 c = coef[q];
+                u.x = fma(c.x, v.x, fma(-c.y, v.y, u.x));
+                u.y = fma(c.x, v.y, fma(c.y, v.x, u.y));
+            }
+        }
+        if (m32) {
+            float cx = 0.f, cy = 0.f;
+            int q = 0;
+            for (; q + 4 <= m32; q += 4) {
+                float2 v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = V32[(size_t)idx32[q + r] * d + i];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 c = coef32[q + r];
+                    cx = fmaf(c.x, v[r].x, fmaf(-c.y, v[r].y, cx));
+                    cy = fmaf(c.x, v[r].y, fmaf(c.y, v[r].x, cy));
+                }
+            }
+            for (; q < m32; ++q) {
+                const float2 v = V32[(size_t)idx32[q] * d + i], c = coef32[q];
+                cx = fmaf(c.x, v.x, fmaf(-c.y, v.y, cx));
+                cy = fmaf(c.x, v.y, fmaf(c.y, v.x, cy));
+            }
+            u.x += (double)cx;
+            u.y += (double)cy;
         }
         o[i] = u;
         acc[0] = fma(u.x, u.x, fma(u.y, u.y, acc[0]));
