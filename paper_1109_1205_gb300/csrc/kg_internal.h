@@ -146,6 +146,7 @@ struct ColDesc {
     float2* V32;            // [M+1][d] V_k truncated to FP32 (or null)
     longlong2* Xf;          // [d] fixed-point image of the next H*psi input (or null)
     double2* W;             // [d] H v workspace
+    double2* U;             // [d] W - a_j v_j, left by the Gram-Schmidt dots
     double* part;           // [nblk_max][kPart] partial sums of this column
     double2* out;           // where the combination writes (V_0 by default)
     const double2* ov;      // n_ov overlap vectors, stride ov_stride
@@ -315,6 +316,16 @@ __device__ __forceinline__ double2 cdotmul(double2 a, double2 b) {
 __device__ __forceinline__ void split_index(const SecView& S, int s, int& i_dn, int& i_up) {
     i_dn = (int)((__umulhi((unsigned)s, S.du_m) + (unsigned)s) >> S.du_l);
     i_up = s - i_dn * S.Du;
+}
+
+// FP32 -> FP64 (exact) on the integer pipe; subnormal inputs give 0.
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e8 = (b >> 23) & 0xffu;
+    if (e8 == 0u) return 0.0;
+    const unsigned e11 = e8 == 0xffu ? 0x7ffu : e8 + 896u;
+    const unsigned hi = (b & 0x80000000u) | (e11 << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 // FP64 -> FP32 by truncation on the integer pipe (no FP64 instruction):

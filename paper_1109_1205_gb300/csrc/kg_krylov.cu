@@ -107,7 +107,7 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         K.Sbuf = nullptr;
         K.V32buf = nullptr;
     }
-    KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * nw));
+    KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * 2 * nw));
     if (nx) KG_CUDA(cudaMalloc(&K.Xfbuf, sizeof(longlong2) * nx));
     KG_CUDA(cudaMalloc(&K.partbuf, sizeof(double) * np));
     KG_CUDA(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B));
@@ -129,6 +129,7 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
             ox += (size_t)D.d;
         }
         D.W = K.Wbuf + ow;
+        D.U = K.Wbuf + nw + ow;
         D.part = K.partbuf + op;
         D.out = D.V;
         ov += (size_t)(M + 1) * D.d;
@@ -292,6 +293,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
 #pragma unroll
     for (int k = 0; k < 3 * KH; ++k) acc[k] = 0.0;
     const bool three = D.S != nullptr;
+    // the last chunk of a first pass leaves u = W - a_j v_j in U for the update
+    const bool keep = !second && k0 + NK == j + 1 && grp == 0;
+    double2* wu = D.U;
     if (three) {
         const double* Sb = D.S + (size_t)(k0 + kb) * d;
         for (int i = blk * TG + t; i < d; i += nblk * TG) {
@@ -300,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
                 const double2 p = vj[i];
                 u.x = fma(-aj, p.x, u.x);
                 u.y = fma(-aj, p.y, u.y);
+                if (keep) wu[i] = u;
             }
             const double dmc = u.y - u.x;
 #pragma unroll
@@ -322,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
                 u.x = fma(-aj, p.x, u.x);
                 u.y = fma(-aj, p.y, u.y);
             }
+            if (keep) wu[i] = u;
 #pragma unroll
             for (int k = 0; k < KH; ++k) {
                 if (k < kn) {
@@ -443,9 +449,12 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     float2* V32_1 = D.V32 ? D.V32 + (size_t)(j + 1) * d : nullptr;
     double acc[1] = {0.0};
     int em = 0;
+    // after a first-pass Gram-Schmidt (level >= 1) U holds W - a_j v_j
+    const bool sub = !second && level < 1;
+    const double2* win = (!second && level >= 1) ? D.U : w;
     auto element = [&](int i) {
-        double2 u = w[i];
-        if (!second) {
+        double2 u = win[i];
+        if (sub) {
             const double2 p = vj[i];
             u.x = fma(-aj, p.x, u.x);
             u.y = fma(-aj, p.y, u.y);
@@ -484,8 +493,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
             u.x -= fma(c.x, v.x, -c.y * v.y);
             u.y -= fma(c.x, v.y, c.y * v.x);
         }
-        u.x -= (double)cx;
-        u.y -= (double)cy;
+        u.x -= f32_to_f64_int(cx);
+        u.y -= f32_to_f64_int(cy);
         out[i] = u;
         if (S1) {
             S1[i] = u.x + u.y;
