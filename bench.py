@@ -293,6 +293,12 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(args.cpu_seconds)
 
+    # ---- the batched and adjoint forms against the plain GPU path
+    batched = adjoint = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        batched = batched_vs_plain(args.batch_instances, args.batch_steps)
+        adjoint = adjoint_vs_fd()
+
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -309,11 +315,102 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "hpsi": hpsi,
             "fp64_tflops_measured": round(fp64, 3), "cpu_baseline": cpu, "clocks": clocks,
             "setup_s": round(t_setup, 2), "E0_ini": E0, "gs_resid": res,
+            "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def batched_vs_plain(n_inst, n_steps):
+    """Equilibrium G_imp of the first n_inst star instances of the batched
+    workload (256 instances, L in [6, 12], random fillings; dt = 0.05, M = 20,
+    orbital (0, up)), once through kg_green_equilibrium_batched and once
+    instance by instance through kg_green_equilibrium.  Ground states are
+    computed beforehand (untimed, the same for both); each path is run once
+    untimed first (work lists, graphs, autotuning), then timed."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c4()
+    models = cfg["models"][:n_inst]
+    opts = kg.kg_opts_default(M=cfg["M"])
+    secs = [kg.Sector(m) for m in models]
+    ok = []
+    for s in secs:
+        try:
+            s.ground_state(opts)
+            ok.append(s)
+        except kg.KGError:
+            pass  # degenerate ground state: left out of both paths
+    orbs, dt = cfg["orbitals"], cfg["dt"]
+    def has_neighbour(s, dag):
+        try:
+            return s.neighbour_dim(0, dag) > 0
+        except kg.KGError:
+            return False  # full or empty up band: that part of G is zero
+
+    gsteps = sum(sum(1 for dag in (False, True) if has_neighbour(s, dag)) * n_steps for s in ok)
+    kg.kg_green_equilibrium_batched([s.handle for s in ok], orbs, dt, n_steps, opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gb, Lb, st = kg.kg_green_equilibrium_batched([s.handle for s in ok], orbs, dt, n_steps, opts)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    for s in ok[:4]:
+        s.green_equilibrium(orbs, dt, n_steps, opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    err = 0.0
+    for i, s in enumerate(ok):
+        g, l = s.green_equilibrium(orbs, dt, n_steps, opts)
+        err = max(err, float(np.max(np.abs(g - Gb[i]))), float(np.max(np.abs(l - Lb[i]))))
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    return {"workload": "first %d of 256 star-SIAM instances (L 6..12, random fillings, seed 20240501), "
+                        "%d steps of dt=0.05, M=20, orbital (0,up), G^> and G^<" % (n_inst, n_steps),
+            "instances": len(ok), "gsteps": gsteps, "unit": "G-steps/s",
+            "batched_value": round(gsteps / tb, 1), "plain_value": round(gsteps / tp, 1),
+            "batched_s": round(tb, 3), "plain_s": round(tp, 3), "speedup": round(tp / tb, 2),
+            "max_abs_diff": err}
+
+
+def adjoint_vs_fd():
+    """Gradient of the bath-fitting loss sum_t |G_imp(t) - G_target(t)|^2 on the
+    star L = 10 (5,5) workload (d = 63,504, 401 times, checkpoints every 20
+    steps) with respect to the 19 parameters (eps_k, V_k, U): one adjoint
+    (kg_green_equilibrium_vjp) against the 38 forward solves of central
+    differences.  Each timed call builds its sector (ground state included)."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c5()
+    orbs, dt, n = cfg["orbitals"], cfg["dt"], cfg["n_steps"]
+    opts = kg.kg_opts_default(M=cfg["M"])
+    Tg, Tl = kg.Sector(cfg["target"]).green_equilibrium(orbs, dt, n, opts)
+    T = (Tg - Tl)[:, 0, 0]
+    kg.Sector(cfg["start"]).green_equilibrium(orbs, dt, n, opts)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gg, Gl = kg.Sector(cfg["start"]).green_equilibrium(orbs, dt, n, opts)
+    tf = time.perf_counter() - t0
+    r = 2.0 * ((Gg - Gl)[:, 0, 0] - T)
+    dGg = np.zeros_like(Gg)
+    dGl = np.zeros_like(Gl)
+    dGg[:, 0, 0] = r
+    dGl[:, 0, 0] = -r
+    t0 = time.perf_counter()
+    s = kg.Sector(cfg["start"])
+    kg.kg_green_equilibrium_vjp(s.handle, 10, orbs, dt, n, dGg, dGl, opts, checkpoint=cfg["checkpoint"])
+    tv = time.perf_counter() - t0
+    return {"workload": "star SIAM L=10 (5,5) d=63504, 401 times dt=0.05, M=20, checkpoints every 20 steps, "
+                        "19 fitted parameters", "forward_s": round(tf, 3), "vjp_s": round(tv, 3),
+            "vjp_over_forward": round(tv / tf, 2), "fd_forwards": 38, "speedup_vs_fd": round(38 * tf / tv, 2)}
 
 
 def cpu_baseline_sample(budget_s):
@@ -402,6 +499,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-gsteps", type=int, default=4)
     ap.add_argument("--ncu-case", action="store_true", help="small case for full ncu captures")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint comparisons")
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=100)
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)
