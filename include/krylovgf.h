@@ -71,9 +71,13 @@ typedef struct kg_opts {
                            Gram-Schmidt pass against every stored Lanczos
                            vector; 2: plus two passes (1)                       */
     int batch;          /* columns per batched propagation launch, 0 = all (0) */
-    int schedule;       /* H*psi hop sums: 0 = exact 64-bit integer sums when
-                           all hops share one amplitude (else FP64), 1 = FP64
-                           sums always (0)                                      */
+    int schedule;       /* bit 0: H*psi hop sums in FP64 always, instead of
+                           exact 64-bit integer sums when all hops share one
+                           amplitude; bit 1: each propagation step's
+                           exponential e^{-iT tau} e_1 through the eigen-
+                           decomposition of T (Section 3, Eq. (udelta)),
+                           instead of the scaled Taylor series of the same
+                           vector (0)                                           */
     int use_graphs;     /* replay each propagation step as a CUDA graph (1)    */
     double dt_internal; /* Keldysh: Krylov step inside one grid step; 0 = dt   */
     unsigned long long seed; /* ground-state start vector seed (1234)         */

@@ -441,8 +441,8 @@ int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, in
             // ---- forward pass: checkpoints and the overlaps (for dL/dE0)
             Krylov KF, KB;
             std::vector<const kg_sector*> cols(na, nb);
-            if (rc == KG_OK) rc = krylov_alloc(KF, cols, std::min(o->M, dn), s->nsm, o->schedule != 1);
-            if (rc == KG_OK) rc = krylov_alloc(KB, cols, std::min(o->M, dn), s->nsm, o->schedule != 1);
+            if (rc == KG_OK) rc = krylov_alloc(KF, cols, std::min(o->M, dn), s->nsm, o->schedule);
+            if (rc == KG_OK) rc = krylov_alloc(KB, cols, std::min(o->M, dn), s->nsm, o->schedule);
             if (rc == KG_OK) {
                 for (int a = 0; a < na; ++a) {
                     ColDesc& D = KF.hdesc[a];

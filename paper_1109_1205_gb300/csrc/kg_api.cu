@@ -14,7 +14,7 @@ int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o
         set_error("NULL vector or negative step count");
         return KG_EINVAL;
     }
-    if (o->M < 1 || o->M > kMaxM || o->reorth < 0 || o->reorth > 2) {
+    if (o->M < 1 || o->M > kMaxM || o->reorth < 0 || o->reorth > 2 || o->schedule < 0 || o->schedule > 3) {
         set_error("bad M or reorth");
         return KG_EINVAL;
     }
@@ -23,7 +23,7 @@ int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o
     const int d = (int)s->d;
     Krylov K;
     StepRunner R;
-    int rc = krylov_alloc(K, {s}, std::min(o->M, d), s->nsm, o->schedule != 1);
+    int rc = krylov_alloc(K, {s}, std::min(o->M, d), s->nsm, o->schedule);
     if (rc == KG_OK) {
         K.hdesc[0].tau = dt;
         rc = krylov_upload(K, st);

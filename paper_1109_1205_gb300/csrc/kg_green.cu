@@ -98,6 +98,10 @@ static int check_opts(const kg_opts* o) {
         set_error("reorth must be 0, 1 or 2");
         return KG_EINVAL;
     }
+    if (o->schedule < 0 || o->schedule > 3) {
+        set_error("schedule must be in [0, 3]");
+        return KG_EINVAL;
+    }
     return KG_OK;
 }
 
@@ -276,7 +280,7 @@ static int green_eq_batch(kg_sector* const* sv, int n_inst, const int* orb, int 
     // breakdown (the recursion is exact once it spans the sector)
     const int Mb = o->M;
     Krylov K;
-    int rc = krylov_alloc(K, cols, Mb, inst[0]->nsm, o->schedule != 1);
+    int rc = krylov_alloc(K, cols, Mb, inst[0]->nsm, o->schedule);
     size_t n_ov = 0;
     for (auto& g : G) {
         const size_t na = g.idx.size();
@@ -485,7 +489,7 @@ static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
     if (B.ready) return KG_OK;
     const int na = (int)B.idx.size(), dn = (int)B.nb->d;
     std::vector<const kg_sector*> cols(na, B.nb);
-    KG_TRY(krylov_alloc(B.K, cols, std::min(X->o.M, dn), X->fin->nsm, X->o.schedule != 1));
+    KG_TRY(krylov_alloc(B.K, cols, std::min(X->o.M, dn), X->fin->nsm, X->o.schedule));
     for (auto& D : B.K.hdesc) D.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
     KG_TRY(krylov_upload(B.K, st));
     KG_CUDA(cudaMalloc(&B.store, sizeof(double2) * (size_t)X->n_t * na * dn));
@@ -576,7 +580,7 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
     if (n_t > 1) {
         Krylov K;
         StepRunner R;
-        int rc = krylov_alloc(K, {fin}, std::min(o->M, (int)d), fin->nsm, o->schedule != 1);
+        int rc = krylov_alloc(K, {fin}, std::min(o->M, (int)d), fin->nsm, o->schedule);
         if (rc == KG_OK) {
             K.hdesc[0].tau = dt / X->n_sub;
             rc = krylov_upload(K, st);

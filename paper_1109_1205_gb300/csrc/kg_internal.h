@@ -165,6 +165,7 @@ struct ColDesc {
 // phase covers every column of the batch in about one wave.
 struct Krylov {
     int B = 0, M = 0, nsm = 148;
+    int schedule = 0;               // kg_opts.schedule bits (hop sums, step exponential)
     long long total_d = 0;
     double wave_scale = 1.0;        // work-list size relative to one wave (tuned)
     std::vector<ColDesc> hdesc;     // host copy (device addresses)
@@ -187,9 +188,11 @@ struct Krylov {
     int dim(int b) const { return hdesc[b].d; }
 };
 
-// One column per entry of `cols` (sectors may repeat).  int_hops selects the
-// exact integer hop sums for sectors with uniform hopping.
-int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, bool int_hops);
+// One column per entry of `cols` (sectors may repeat).  schedule: the
+// kg_opts.schedule bits (bit 0: FP64 hop sums instead of the exact integer
+// sums for sectors with uniform hopping; bit 1: step exponential through the
+// eigen-decomposition of T instead of the Taylor series).
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule);
 int krylov_upload(Krylov& K, cudaStream_t st);  // after editing hdesc (tau, out, overlaps)
 void krylov_free(Krylov& K);
 int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n, int group = -1);

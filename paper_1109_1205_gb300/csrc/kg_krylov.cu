@@ -25,8 +25,10 @@
 namespace kg {
 
 // ------------------------------------------------------------ workspace
-int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, bool int_hops) {
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule) {
     K = Krylov();
+    K.schedule = schedule;
+    const bool int_hops = !(schedule & 1);
     K.B = (int)cols.size();
     K.M = M;
     K.nsm = nsm;
@@ -735,9 +737,122 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
     }
 }
 
+// ------------------------------------ step exponential by a Taylor series
+// c = beta0 e^{-i T tau} e_1 (times s_k per component), the vector of
+// Eq. (udelta), without the eigen-decomposition: the series in (-i T h)
+// with h = tau / n_sub and n_sub chosen so that |T h| <= 1/2 (Gershgorin
+// bound), 18 terms per sub-step (remainder below 1e-22 of the sum).  One
+// warp per column; lane l holds components l and l + 32 (R = 2), so every
+// FP64 instruction serves the whole vector -- the eigen-decomposition's
+// bulge chase is serial.  Modes 0 and 2 as in k_tridiag.
+constexpr int kTaylorTerms = 18;
+
+template <int R>
+__device__ __forceinline__ void tri_apply(const double (&a)[R], const double (&bl)[R], const double (&br)[R],
+                                          const double2 (&x)[R], double2 (&y)[R], int lane) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        // x_{k-1} and x_{k+1} for k = lane + 32 r
+        double2 xm, xp;
+        xm.x = __shfl_up_sync(0xffffffffu, x[r].x, 1);
+        xm.y = __shfl_up_sync(0xffffffffu, x[r].y, 1);
+        xp.x = __shfl_down_sync(0xffffffffu, x[r].x, 1);
+        xp.y = __shfl_down_sync(0xffffffffu, x[r].y, 1);
+        const double2 lo = r > 0 ? x[r > 0 ? r - 1 : 0] : make_double2(0.0, 0.0);
+        const double2 hi = r + 1 < R ? x[r + 1 < R ? r + 1 : r] : make_double2(0.0, 0.0);
+        const double lox = __shfl_sync(0xffffffffu, lo.x, 31), loy = __shfl_sync(0xffffffffu, lo.y, 31);
+        const double hix = __shfl_sync(0xffffffffu, hi.x, 0), hiy = __shfl_sync(0xffffffffu, hi.y, 0);
+        if (lane == 0) xm = make_double2(lox, loy);
+        if (lane == 31) xp = make_double2(hix, hiy);
+        y[r].x = fma(a[r], x[r].x, fma(bl[r], xm.x, br[r] * xp.x));
+        y[r].y = fma(a[r], x[r].y, fma(bl[r], xm.y, br[r] * xp.y));
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * kTriWarps) k_texp(const ColDesc* desc, ColScalars* cs, int B, int Mcap,
+                                                        int mode, const double* taus, int ntau, double2* cq) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * kTriWarps + warp;
+    if (b >= B) return;
+    ColScalars* C = cs + b;
+    const int m = C->m_eff;
+    if (m == 0) {
+        for (int k = lane; k < Mcap; k += 32) C->c[k] = make_double2(0.0, 0.0);
+        if (mode == 2)
+            for (int t = 0; t < ntau; ++t)
+                for (int k = lane; k < Mcap; k += 32) cq[((size_t)b * ntau + t) * Mcap + k] = make_double2(0.0, 0.0);
+        return;
+    }
+    double a[R], bl[R], br[R];
+    double g = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = lane + 32 * r;
+        a[r] = k < m ? C->alpha[k] : 0.0;
+        bl[r] = (k < m && k >= 1) ? C->beta[k] : 0.0;      // couples k-1 and k
+        br[r] = (k + 1 < m) ? C->beta[k + 1] : 0.0;         // couples k and k+1
+        g = fmax(g, fabs(a[r]) + fabs(bl[r]) + fabs(br[r]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    const double beta0 = C->beta0;
+    const int nt = mode == 0 ? 1 : ntau;
+    for (int t = 0; t < nt; ++t) {
+        const double tau = mode == 0 ? desc[b].tau : taus[(size_t)b * ntau + t];
+        const int nsub = max(1, (int)ceil(2.0 * g * fabs(tau)));
+        const double h = tau / nsub;
+        double2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = make_double2((lane + 32 * r) == 0 ? 1.0 : 0.0, 0.0);
+        for (int sub = 0; sub < nsub; ++sub) {
+            double2 term[R], sum[R], y[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) term[r] = sum[r] = v[r];
+            for (int n = 1; n <= kTaylorTerms; ++n) {
+                tri_apply<R>(a, bl, br, term, y, lane);
+                const double f = h / n;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    term[r] = make_double2(f * y[r].y, -f * y[r].x);  // (-i h / n) T term
+                    sum[r].x += term[r].x;
+                    sum[r].y += term[r].y;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = sum[r];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = lane + 32 * r;
+            if (k < m) {
+                const double sc = beta0 * C->scale[k];
+                const double2 cv = make_double2(sc * v[r].x, sc * v[r].y);
+                if (mode == 0)
+                    C->c[k] = cv;
+                else
+                    cq[((size_t)b * ntau + t) * Mcap + k] = cv;
+            } else if (k < Mcap && mode == 2) {
+                cq[((size_t)b * ntau + t) * Mcap + k] = make_double2(0.0, 0.0);
+            }
+        }
+    }
+}
+
+static int launch_texp(Krylov& K, int mode, const double* taus, int ntau, double2* cq, cudaStream_t st) {
+    const int nb = (K.B + kTriWarps - 1) / kTriWarps;
+    if (K.M <= 32)
+        k_texp<1><<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, mode, taus, ntau, cq);
+    else
+        k_texp<2><<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, mode, taus, ntau, cq);
+    KG_LAUNCHED();
+    return KG_OK;
+}
+
 int launch_tridiag(Krylov& K, int mode, cudaStream_t st) {
     const int nb = (K.B + kTriWarps - 1) / kTriWarps;
     ProfScope ps("tridiag", st);
+    if (mode == 0 && !(K.schedule & 2)) return launch_texp(K, 0, nullptr, 0, nullptr, st);
     k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, mode, nullptr, 0, nullptr);
     KG_LAUNCHED();
     return KG_OK;
@@ -926,6 +1041,7 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
 int launch_tridiag_multi(Krylov& K, const double* taus, int ntau, double2* cq, cudaStream_t st) {
     const int nb = (K.B + kTriWarps - 1) / kTriWarps;
     ProfScope ps("tridiag", st);
+    if (!(K.schedule & 2)) return launch_texp(K, 2, taus, ntau, cq, st);
     k_tridiag<<<nb, 32 * kTriWarps, 0, st>>>(K.desc, K.cs, K.B, K.M, K.Q, 2, taus, ntau, cq);
     KG_LAUNCHED();
     return KG_OK;
@@ -989,7 +1105,7 @@ int ground_state(kg_sector* s, const kg_opts* o) {
     const int M = std::max(1, std::min(o->M_gs, d));
     if (!s->gs) KG_CUDA(cudaMalloc(&s->gs, sizeof(double2) * d));
     Krylov K;
-    int rc = krylov_alloc(K, {s}, M, s->nsm, o->schedule != 1);
+    int rc = krylov_alloc(K, {s}, M, s->nsm, o->schedule);
     if (rc != KG_OK) {
         krylov_free(K);
         return rc;

@@ -187,10 +187,12 @@ def test_propagate_parity(reorth, dt, n):
     assert abs(np.linalg.norm(y) - 1) < 1e-12
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
 def test_hop_sum_schedules(schedule):
-    """Exact integer hop sums (schedule 0) and FP64 hop sums (schedule 1) on
-    uniform-hopping models, through propagation and the ground state."""
+    """Exact integer hop sums (schedule bit 0 clear) and FP64 hop sums (bit 0
+    set), with the step exponential by Taylor series (bit 1 clear) or by the
+    eigen-decomposition of T (bit 1 set), on uniform-hopping models, through
+    propagation and the ground state."""
     for model in (W.hubbard_ring(10, 4.0, 5, 4), W.siam_chain(9, 3.0, 4, 5, field=0.7)):
         s = kg.Sector(model)
         o = oracle.Sector(model)
@@ -231,6 +233,32 @@ def test_propagate_large_sector_and_graphs():
         xd = dev(x)
         s.propagate(xd, 0.05, 8, kg.kg_opts_default(use_graphs=graphs))
         assert np.max(np.abs(host(xd) - o.propagate(x, 0.4))) < 1e-11
+
+
+@pytest.mark.parametrize("M", [12, 40])
+def test_step_exponential_taylor_vs_eigen(M):
+    """The two forms of e^{-iT tau} e_1 (scaled Taylor series; implicit-QR
+    eigen-decomposition) agree to rounding, with M on both sides of 32 (one
+    or two components per lane) and a step large enough for sub-steps."""
+    m = W.random_model(7, 3, 3, seed=17, complex_hopping=True)
+    s = kg.Sector(m)
+    x = W.random_state(s.dim, 8)
+    out = []
+    for schedule in (0, 2):
+        xd = dev(x)
+        s.propagate(xd, 0.3, 4, kg.kg_opts_default(M=M, schedule=schedule))
+        out.append(host(xd))
+    # same Krylov spaces, so the two agree to rounding whatever M is
+    assert np.max(np.abs(out[0] - out[1])) < 1e-12
+    if M == 40:  # and with enough Krylov vectors, with the oracle
+        ref = oracle.Sector(m).propagate(x, 1.2)
+        assert np.max(np.abs(out[0] - ref)) < 1e-11
+
+
+def test_bad_schedule_rejected():
+    s = kg.Sector(W.random_model(4, 2, 2, seed=1))
+    with pytest.raises(kg.KGError):
+        s.green_equilibrium([(0, 0)], 0.1, 2, kg.kg_opts_default(schedule=4))
 
 
 # ------------------------------------------------------- equilibrium G
