@@ -532,6 +532,34 @@ int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, in
                 rc = krylov_upload(KF, st);
             }
             if (rc == KG_OK) rc = RS.init(KF, o->reorth, st, o->use_graphs != 0);
+            // The Krylov spaces that the segment's forward steps build are
+            // kept (basis and scalars per step) when the memory is there, so
+            // that the backward sweep reads them instead of rebuilding them.
+            const int MK = KF.M + 1;
+            double2* segV = nullptr;
+            ColScalars* segC = nullptr;
+            if (rc == KG_OK &&
+                (cudaMalloc(&segV, sizeof(double2) * (size_t)Kc * na * MK * dn) != cudaSuccess ||
+                 cudaMalloc(&segC, sizeof(ColScalars) * (size_t)Kc * na) != cudaSuccess)) {
+                cudaGetLastError();
+                cudaFree(segV);
+                cudaFree(segC);
+                segV = nullptr;
+                segC = nullptr;
+            }
+            if (segV) frees.push_back(segV);
+            if (segC) frees.push_back(segC);
+            std::vector<double2*> baseV(na);
+            for (int a = 0; a < na; ++a) baseV[a] = KF.hdesc[a].V;
+            auto point_kf = [&](int step) -> int {  // step < 0: KF's own basis
+                for (int a = 0; a < na; ++a)
+                    KF.hdesc[a].V = step < 0 ? baseV[a] : segV + ((size_t)step * na + a) * MK * dn;
+                KG_TRY(krylov_upload(KF, st));
+                if (step >= 0)
+                    KG_CUDA(cudaMemcpyAsync(KF.cs, segC + (size_t)step * na, sizeof(ColScalars) * na,
+                                            cudaMemcpyDeviceToDevice, st));
+                return KG_OK;
+            };
             for (int c = (n_steps - 1) / Kc; rc == KG_OK && c >= 0 && n_steps > 0; --c) {
                 const int k0 = c * Kc, k1 = std::min(n_steps, k0 + Kc);
                 rc = load(KF, ckpt + (size_t)c * na * dn);
@@ -539,12 +567,32 @@ int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, in
                 for (int k = k0 + 1; rc == KG_OK && k <= k1; ++k) {
                     rc = RS.run(st);
                     if (rc == KG_OK) rc = save(KF, seg + (size_t)(k - k0) * na * dn);
+                    if (rc == KG_OK && segV) {
+                        // basis of the step k-1 -> k: v_0 = psi_{k-1}, then V_1..V_M as built
+                        const int sidx = k - 1 - k0;
+                        for (int a = 0; rc == KG_OK && a < na; ++a) {
+                            double2* dst = segV + ((size_t)sidx * na + a) * MK * dn;
+                            if (cudaMemcpyAsync(dst, seg + (size_t)sidx * na * dn + (size_t)a * dn,
+                                                sizeof(double2) * dn, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                                cudaMemcpyAsync(dst + dn, KF.vec(a, 1), sizeof(double2) * (size_t)(MK - 1) * dn,
+                                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                                rc = KG_ECUDA;
+                        }
+                        if (rc == KG_OK &&
+                            cudaMemcpyAsync(segC + (size_t)sidx * na, KF.cs, sizeof(ColScalars) * na,
+                                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                            rc = KG_ECUDA;
+                    }
                 }
                 for (int k = k1; rc == KG_OK && k > k0; --k) {
                     rc = bra_part(k, seg + (size_t)(k - k0) * na * dn);
                     // forward space of psi_{k-1}: node vectors u_q
-                    if (rc == KG_OK) rc = load(KF, seg + (size_t)(k - 1 - k0) * na * dn);
-                    if (rc == KG_OK) rc = build_space(KF, o->reorth, st);
+                    if (segV) {
+                        if (rc == KG_OK) rc = point_kf(k - 1 - k0);
+                    } else {
+                        if (rc == KG_OK) rc = load(KF, seg + (size_t)(k - 1 - k0) * na * dn);
+                        if (rc == KG_OK) rc = build_space(KF, o->reorth, st);
+                    }
                     if (rc == KG_OK) rc = launch_tridiag_multi(KF, tauF, nq, cqF, st);
                     if (rc == KG_OK) {
                         k_lincomb<<<dim3(grid_for(dn), na), kThreads, 0, st>>>(KF.desc, KF.cs, KF.M, cqF, nq, Uq);
@@ -569,6 +617,7 @@ int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, in
                                  : KG_ECUDA;
                     if (rc == KG_OK) rc = sources(k - 1, lam);
                 }
+                if (rc == KG_OK && segV) rc = point_kf(-1);  // the step graph reads KF's own basis
             }
             RS.release();
             if (rc == KG_OK) rc = bra_part(0, chi);
