@@ -94,33 +94,45 @@ __device__ __forceinline__ void hop_sum(const SecView& S, const double2* __restr
     }
 }
 
-// Conditional negation without a branch: m is 0 or -1.
-__device__ __forceinline__ long long neg_if(long long v, long long m) { return (v ^ m) - m; }
-
 // Hop part of (H x)[i_dn, i_up] from the fixed-point image Xf of x (all
 // components on one exponent, written by the kernel that produced x): the
 // same signed sums as the on-the-fly path, without the conversions.
 __device__ __forceinline__ void hop_sum_pre(const SecView& S, const longlong2* __restrict__ Xf, int i_dn, int i_up,
                                             long long& ix, long long& iy) {
-    const int u0 = __ldg(S.up_off + i_up), u1 = __ldg(S.up_off + i_up + 1);
-    const int d0 = __ldg(S.dn_off + i_dn), d1 = __ldg(S.dn_off + i_dn + 1);
+    // each string's hop list holds its +1-sign hops first, then the -1 ones
+    const int u0 = __ldg(S.up_off + i_up), us = __ldg(S.up_split + i_up), u1 = __ldg(S.up_off + i_up + 1);
+    const int d0 = __ldg(S.dn_off + i_dn), ds = __ldg(S.dn_split + i_dn), d1 = __ldg(S.dn_off + i_dn + 1);
     const longlong2* row = Xf + (size_t)i_dn * S.Du;
+    const longlong2* col = Xf + i_up;
+    const unsigned* upx = reinterpret_cast<const unsigned*>(S.up_ent);  // .x of entry e at [2e]
+    const unsigned* dnx = reinterpret_cast<const unsigned*>(S.dn_ent);
+    long long px = 0, py = 0, nx = 0, ny = 0;
 #pragma unroll 4
-    for (int e = u0; e < u1; ++e) {
-        const uint2 en = __ldg(S.up_ent + e);
-        const longlong2 v = row[en.x];
-        const long long m = -(long long)(en.y >> 31);
-        ix += neg_if(v.x, m);
-        iy += neg_if(v.y, m);
+    for (int e = u0; e < us; ++e) {
+        const longlong2 v = row[__ldg(upx + 2 * e)];
+        px += v.x;
+        py += v.y;
     }
 #pragma unroll 4
-    for (int e = d0; e < d1; ++e) {
-        const uint2 en = __ldg(S.dn_ent + e);
-        const longlong2 v = Xf[(size_t)en.x * S.Du + i_up];
-        const long long m = -(long long)(en.y >> 31);
-        ix += neg_if(v.x, m);
-        iy += neg_if(v.y, m);
+    for (int e = us; e < u1; ++e) {
+        const longlong2 v = row[__ldg(upx + 2 * e)];
+        nx += v.x;
+        ny += v.y;
     }
+#pragma unroll 4
+    for (int e = d0; e < ds; ++e) {
+        const longlong2 v = col[(size_t)__ldg(dnx + 2 * e) * S.Du];
+        px += v.x;
+        py += v.y;
+    }
+#pragma unroll 4
+    for (int e = ds; e < d1; ++e) {
+        const longlong2 v = col[(size_t)__ldg(dnx + 2 * e) * S.Du];
+        nx += v.x;
+        ny += v.y;
+    }
+    ix += px - nx;
+    iy += py - ny;
 }
 
 // v * 2^(E - 1075 - P) rounded to nearest (ties to even), assembled on the
@@ -186,6 +198,33 @@ __global__ void __launch_bounds__(kThreads) k_maxexp(const double2* __restrict__
     }
     m = block_max_int(m, sm);
     if (threadIdx.x == 0) atomicMax(emax, m);
+}
+
+// Fixed-point image of x on the exponent *emax (for the exact hop sums).
+__global__ void __launch_bounds__(kThreads) k_tofix(const double2* __restrict__ x, int d, const int* emax, int P,
+                                                    longlong2* __restrict__ xf) {
+    const int E = *emax;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        xf[i] = make_longlong2(fix_term(v.x, E, P, 0u), fix_term(v.y, E, P, 0u));
+    }
+}
+
+// y = H x with the hop sums read from the fixed-point image xf of x.
+__global__ void __launch_bounds__(kThreads) k_hpsi_pre(SecView S, const double2* __restrict__ x,
+                                                       const longlong2* __restrict__ xf, double2* __restrict__ y,
+                                                       const int* emax) {
+    const int E = *emax;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S.d; idx += gridDim.x * blockDim.x) {
+        int i_dn, i_up;
+        split_index(S, idx, i_dn, i_up);
+        const double2 xv = x[idx];
+        const double diag = __ldg(S.diag + idx);
+        long long ix = 0, iy = 0;
+        hop_sum_pre(S, xf, i_dn, i_up, ix, iy);
+        y[idx] = make_double2(fma(diag, xv.x, S.h0 * fix_to_double(ix, E, S.fix_pre)),
+                              fma(diag, xv.y, S.h0 * fix_to_double(iy, E, S.fix_pre)));
+    }
 }
 
 template <int MODE>
@@ -317,16 +356,27 @@ int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::max(1, std::min((S.d + kThreads - 1) / kThreads, nsm * 8));
     if (S.hopmode == 0 && S.fix_pre >= 0) {
-        // largest exponent of x first (one extra read of x), then exact hop sums
-        static thread_local int* d_emax = nullptr;
-        if (!d_emax) KG_CUDA(cudaMalloc(&d_emax, sizeof(int)));
+        // largest exponent of x, the fixed-point image of x on it (stream-
+        // ordered scratch, so calls on different streams do not share it),
+        // then exact hop sums that add the image's integers
         ProfScope ps("hpsi", st);
-        KG_CUDA(cudaMemsetAsync(d_emax, 0, sizeof(int), st));
-        k_maxexp<<<std::min(nb, nsm * 4), kThreads, 0, st>>>(x, S.d, d_emax);
-        KG_LAUNCHED();
-        k_hpsi<3><<<nb, kThreads, 0, st>>>(S, x, y, d_emax);
-        KG_LAUNCHED();
-        return KG_OK;
+        char* scratch = nullptr;
+        const size_t off = 256;  // the exponent, then the image (16-byte aligned)
+        KG_CUDA(cudaMallocAsync((void**)&scratch, off + sizeof(longlong2) * (size_t)S.d, st));
+        int* d_emax = reinterpret_cast<int*>(scratch);
+        longlong2* xf = reinterpret_cast<longlong2*>(scratch + off);
+        int rc = KG_OK;
+        if (cudaMemsetAsync(d_emax, 0, sizeof(int), st) != cudaSuccess) rc = KG_ECUDA;
+        if (rc == KG_OK) {
+            k_maxexp<<<std::min(nb, nsm * 4), kThreads, 0, st>>>(x, S.d, d_emax);
+            k_tofix<<<nb, kThreads, 0, st>>>(x, S.d, d_emax, S.fix_pre, xf);
+            k_hpsi_pre<<<nb, kThreads, 0, st>>>(S, x, xf, y, d_emax);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_fail(e, "kernel launch", __FILE__, __LINE__);
+            else count_launch(3);
+        }
+        cudaFreeAsync(scratch, st);
+        return rc;
     }
     ProfScope ps("hpsi", st);
     if (S.hopmode == 0)

@@ -60,7 +60,8 @@ struct SpinTables {
     int max_row = 0;
     uint32_t* bits = nullptr;  // [D]
     int* off = nullptr;        // [D + 1]
-    uint2* ent = nullptr;      // [nnz]
+    uint2* ent = nullptr;      // [nnz], per string the +1-sign hops first
+    int* split = nullptr;      // [D] first entry of string i with sign -1
     double* e = nullptr;       // [D]  sum over occupied i of (eps_i + h_ii)
 };
 
@@ -71,6 +72,8 @@ struct SecView {
     const uint32_t* dn_bits;
     const int* up_off;
     const uint2* up_ent;
+    const int* up_split;  // first entry of each string's -1-sign hops
+    const int* dn_split;
     const double* up_e;
     const int* dn_off;
     const uint2* dn_ent;

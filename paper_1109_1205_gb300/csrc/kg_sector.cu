@@ -122,20 +122,26 @@ __global__ void k_hop_count(int L, int D, const uint32_t* bits, const uint32_t* 
     cnt[i] = c;
 }
 
+// Entries of string i: the hops with fermion sign +1 first, then those with
+// -1 from split[i] on, so that sign-uniform loops can skip the sign test.
 __global__ void k_hop_fill(int L, int D, const uint32_t* bits, const uint32_t* hnz, const int* off,
-                           uint2* ent) {
+                           uint2* ent, int* split) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= D) return;
     const uint32_t s = bits[i];
     const uint32_t full = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
     int e = off[i];
-    for (uint32_t occ = s; occ; occ &= occ - 1u) {
-        const int a = __ffs(occ) - 1;
-        for (uint32_t emp = hnz[a] & ~s & full; emp; emp &= emp - 1u) {
-            const int b = __ffs(emp) - 1;
-            const uint32_t src = (s & ~(1u << a)) | (1u << b);
-            const uint32_t neg = __popc(s & between_mask(a, b)) & 1u;
-            ent[e++] = make_uint2(rank_string(src), (neg << 31) | (uint32_t)(a * L + b));
+    for (uint32_t want = 0; want < 2; ++want) {
+        if (want == 1) split[i] = e;
+        for (uint32_t occ = s; occ; occ &= occ - 1u) {
+            const int a = __ffs(occ) - 1;
+            for (uint32_t emp = hnz[a] & ~s & full; emp; emp &= emp - 1u) {
+                const int b = __ffs(emp) - 1;
+                const uint32_t neg = __popc(s & between_mask(a, b)) & 1u;
+                if (neg != want) continue;
+                const uint32_t src = (s & ~(1u << a)) | (1u << b);
+                ent[e++] = make_uint2(rank_string(src), (neg << 31) | (uint32_t)(a * L + b));
+            }
         }
     }
 }
@@ -182,9 +188,12 @@ static int build_spin(SpinTables& T, int L, int N, const uint32_t* d_hnz, const 
     T.max_row = mx;
     KG_CUDA(cudaMemcpyAsync(T.off, off.data(), sizeof(int) * (D + 1), cudaMemcpyHostToDevice, st));
     KG_CUDA(cudaMalloc(&T.ent, sizeof(uint2) * (acc > 0 ? acc : 1)));
+    KG_CUDA(cudaMalloc(&T.split, sizeof(int) * D));
     if (acc > 0) {
-        k_hop_fill<<<nb, 256, 0, st>>>(L, D, T.bits, d_hnz, T.off, T.ent);
+        k_hop_fill<<<nb, 256, 0, st>>>(L, D, T.bits, d_hnz, T.off, T.ent, T.split);
         KG_LAUNCHED();
+    } else {
+        KG_CUDA(cudaMemsetAsync(T.split, 0, sizeof(int) * D, st));
     }
     double* d_eps = nullptr;
     KG_CUDA(cudaMalloc(&d_eps, sizeof(double) * L));
@@ -200,6 +209,7 @@ static void free_spin(SpinTables& T) {
     cudaFree(T.bits);
     cudaFree(T.off);
     cudaFree(T.ent);
+    cudaFree(T.split);
     cudaFree(T.e);
     T = SpinTables();
 }
@@ -457,6 +467,8 @@ kg::SecView kg_sector::view() const {
     v.dn_bits = dn.bits;
     v.up_off = up.off;
     v.up_ent = up.ent;
+    v.up_split = up.split;
+    v.dn_split = dn.split;
     v.up_e = up.e;
     v.dn_off = dn.off;
     v.dn_ent = dn.ent;
