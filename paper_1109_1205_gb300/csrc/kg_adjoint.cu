@@ -39,10 +39,11 @@ constexpr int kMaxNodes = 16;
 constexpr int kMaxPairs = 128;
 
 // ------------------------------------------------------- node vectors
-// out[(b*ntau + t)*d + i] = sum_k cq[b][t][k] V_k[i] for the columns of K
-// (all columns of one sector, dimension d).
+// out[outoff[b] + t*d_b + i] = sum_k cq[b][t][k] V_k[i] for every column b
+// of K (columns may differ in dimension d_b).
 __global__ void __launch_bounds__(kThreads) k_lincomb(const ColDesc* desc, const ColScalars* cs, int Mcap,
-                                                      const double2* cq, int ntau, double2* out) {
+                                                      const double2* cq, int ntau, double2* out,
+                                                      const size_t* outoff) {
     __shared__ double2 c[kMaxNodes + 1][kMaxM];
     const int b = blockIdx.y;
     const ColDesc D = desc[b];
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_lincomb(const ColDesc* desc, const
                 acc[t].y = fma(c[t][k].x, v.y, fma(c[t][k].y, v.x, acc[t].y));
             }
         }
-        for (int t = 0; t < ntau; ++t) out[((size_t)b * ntau + t) * D.d + i] = acc[t];
+        for (int t = 0; t < ntau; ++t) out[outoff[b] + (size_t)t * D.d + i] = acc[t];
     }
 }
 
@@ -378,272 +379,344 @@ int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, in
         return KG_OK;
     };
     int rc = KG_OK;
-    for (int spin = 0; spin < 2 && rc == KG_OK; ++spin) {
-        const int na = (int)idx[spin].size();
-        if (!na) continue;
-        for (int dagger = 1; dagger >= 0 && rc == KG_OK; --dagger) {
+    // ---- the (spin, kind) groups of columns, all propagated in the same
+    // launches (like the forward): column b is orbital a of group g, a
+    // vector of that group's neighbour sector
+    struct Group {
+        int spin, dagger, na, dn, col0;
+        kg_sector* nb;
+        double tau;
+        std::vector<int> idx;
+        std::vector<std::complex<double>> Gb, pk;  // cotangent Gbar_{ab,k}, phase p_k
+    };
+    std::vector<Group> grp;
+    for (int spin = 0; spin < 2; ++spin) {
+        if (idx[spin].empty()) continue;
+        for (int dagger = 1; dagger >= 0; --dagger) {
             kg_sector* nb = nullptr;
-            if (neighbour(s, spin, dagger, &nb) != KG_OK) continue;
-            const int dn = (int)nb->d;
-            const double tau = dagger ? dt : -dt;
             const double* dG = dagger ? dGgtr : dGles;
-            if (!dG) continue;
-            // cotangent Gbar_{ab,k} and phase p_k of this group
-            std::vector<std::complex<double>> Gb((size_t)rows * na * na), pk(rows);
+            if (!dG || neighbour(s, spin, dagger, &nb) != KG_OK) continue;
+            Group G;
+            G.spin = spin;
+            G.dagger = dagger;
+            G.na = (int)idx[spin].size();
+            G.dn = (int)nb->d;
+            G.nb = nb;
+            G.tau = dagger ? dt : -dt;
+            G.idx = idx[spin];
+            const int na = G.na;
+            G.Gb.resize((size_t)rows * na * na);
+            G.pk.resize(rows);
             for (int k = 0; k < rows; ++k) {
                 const double t = dt * k;
-                pk[k] = dagger ? std::complex<double>(0, -1) * std::exp(std::complex<double>(0, E0 * t))
-                               : std::complex<double>(0, 1) * std::exp(std::complex<double>(0, -E0 * t));
+                G.pk[k] = dagger ? std::complex<double>(0, -1) * std::exp(std::complex<double>(0, E0 * t))
+                                 : std::complex<double>(0, 1) * std::exp(std::complex<double>(0, -E0 * t));
                 for (int a = 0; a < na; ++a)
                     for (int b = 0; b < na; ++b) {
                         // particle: G^>_{ab}; hole: G^<_{ba} = p <phi_a | psi_b>
-                        const int r = dagger ? idx[spin][a] : idx[spin][b];
-                        const int c = dagger ? idx[spin][b] : idx[spin][a];
+                        const int r = dagger ? G.idx[a] : G.idx[b];
+                        const int c = dagger ? G.idx[b] : G.idx[a];
                         const size_t e = ((size_t)k * n_orb + r) * n_orb + c;
-                        Gb[((size_t)k * na + a) * na + b] = std::complex<double>(dG[2 * e], dG[2 * e + 1]);
+                        G.Gb[((size_t)k * na + a) * na + b] = std::complex<double>(dG[2 * e], dG[2 * e + 1]);
                     }
             }
-            double2 *chi, *ckpt, *seg, *lam, *y, *Uq, *Wq, *ov, *tmp;
-            double2* cqF;
-            double2* cqB;
-            double *tauF, *tauB;
-            const int nck = n_steps / Kc + 1;
-            rc = dalloc((void**)&chi, sizeof(double2) * na * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&ckpt, sizeof(double2) * (size_t)nck * na * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&seg, sizeof(double2) * (size_t)(Kc + 1) * na * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&lam, sizeof(double2) * na * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&y, sizeof(double2) * na * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&Uq, sizeof(double2) * (size_t)na * nq * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&Wq, sizeof(double2) * (size_t)na * (nq + 1) * dn);
-            if (rc == KG_OK) rc = dalloc((void**)&ov, sizeof(double2) * (size_t)na * rows * na);
-            if (rc == KG_OK) rc = dalloc((void**)&tmp, sizeof(double2) * d0);
-            if (rc == KG_OK) rc = dalloc((void**)&cqF, sizeof(double2) * (size_t)na * nq * o->M);
-            if (rc == KG_OK) rc = dalloc((void**)&cqB, sizeof(double2) * (size_t)na * (nq + 1) * o->M);
-            if (rc == KG_OK) rc = dalloc((void**)&tauF, sizeof(double) * na * nq);
-            if (rc == KG_OK) rc = dalloc((void**)&tauB, sizeof(double) * na * (nq + 1));
-            if (rc != KG_OK) break;
-            for (int a = 0; rc == KG_OK && a < na; ++a)
-                rc = launch_cop(s, nb, orb[2 * idx[spin][a]], spin, dagger, s->gs, chi + (size_t)a * dn, st);
-            // node times: forward e^{-iH tau x_q}, backward e^{+iH tau (1-x_q)} and the full step
-            std::vector<double> hF((size_t)na * nq), hB((size_t)na * (nq + 1));
-            for (int a = 0; a < na; ++a) {
-                for (int q = 0; q < nq; ++q) {
-                    hF[(size_t)a * nq + q] = tau * xq[q];
-                    hB[(size_t)a * (nq + 1) + q] = -tau * (1.0 - xq[q]);
-                }
-                hB[(size_t)a * (nq + 1) + nq] = -tau;
-            }
-            if (rc == KG_OK)
-                rc = cudaMemcpyAsync(tauF, hF.data(), sizeof(double) * hF.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                             cudaMemcpyAsync(tauB, hB.data(), sizeof(double) * hB.size(), cudaMemcpyHostToDevice, st) == cudaSuccess
-                         ? KG_OK
-                         : KG_ECUDA;
-            // ---- forward pass: checkpoints and the overlaps (for dL/dE0)
-            Krylov KF, KB;
-            std::vector<const kg_sector*> cols(na, nb);
-            if (rc == KG_OK) rc = krylov_alloc(KF, cols, std::min(o->M, dn), s->nsm, o->schedule);
-            if (rc == KG_OK) rc = krylov_alloc(KB, cols, std::min(o->M, dn), s->nsm, o->schedule);
-            if (rc == KG_OK) {
+            grp.push_back(std::move(G));
+        }
+    }
+    // columns: per-column sector, dimension and offsets into the concatenated buffers
+    std::vector<const kg_sector*> cols;
+    std::vector<int> colg;
+    std::vector<size_t> off;  // element offset of column b in a [tot] buffer
+    size_t tot = 0;
+    for (int g = 0; g < (int)grp.size(); ++g) {
+        grp[g].col0 = (int)cols.size();
+        for (int a = 0; a < grp[g].na; ++a) {
+            cols.push_back(grp[g].nb);
+            colg.push_back(g);
+            off.push_back(tot);
+            tot += (size_t)grp[g].dn;
+        }
+    }
+    const int NC = (int)cols.size();
+    auto gcol = [&](int g) { return off[grp[g].col0]; };  // first element of group g
+    Krylov KF, KB;
+    double2 *chi = nullptr, *ckpt = nullptr, *seg = nullptr, *lam = nullptr, *y = nullptr, *Uq = nullptr,
+            *Wq = nullptr, *ov = nullptr, *tmp = nullptr, *cqF = nullptr, *cqB = nullptr;
+    double *tauF = nullptr, *tauB = nullptr;
+    size_t *offU = nullptr, *offW = nullptr;
+    const int nck = n_steps / Kc + 1;
+    size_t nov = 0;
+    for (auto& G : grp) nov += (size_t)G.na * rows * G.na;
+    if (NC > 0) {
+        rc = dalloc((void**)&chi, sizeof(double2) * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&ckpt, sizeof(double2) * (size_t)nck * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&seg, sizeof(double2) * (size_t)(Kc + 1) * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&lam, sizeof(double2) * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&y, sizeof(double2) * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&Uq, sizeof(double2) * (size_t)nq * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&Wq, sizeof(double2) * (size_t)(nq + 1) * tot);
+        if (rc == KG_OK) rc = dalloc((void**)&ov, sizeof(double2) * nov);
+        if (rc == KG_OK) rc = dalloc((void**)&tmp, sizeof(double2) * d0);
+        if (rc == KG_OK) rc = dalloc((void**)&cqF, sizeof(double2) * (size_t)NC * nq * o->M);
+        if (rc == KG_OK) rc = dalloc((void**)&cqB, sizeof(double2) * (size_t)NC * (nq + 1) * o->M);
+        if (rc == KG_OK) rc = dalloc((void**)&tauF, sizeof(double) * NC * nq);
+        if (rc == KG_OK) rc = dalloc((void**)&tauB, sizeof(double) * NC * (nq + 1));
+        if (rc == KG_OK) rc = dalloc((void**)&offU, sizeof(size_t) * NC);
+        if (rc == KG_OK) rc = dalloc((void**)&offW, sizeof(size_t) * NC);
+    }
+    std::vector<size_t> hOffU(NC), hOffW(NC), ovoff(grp.size());
+    {
+        size_t o2 = 0;
+        for (int g = 0; g < (int)grp.size(); ++g) {
+            ovoff[g] = o2;
+            o2 += (size_t)grp[g].na * rows * grp[g].na;
+        }
+    }
+    std::vector<double> hF((size_t)NC * nq), hB((size_t)NC * (nq + 1));
+    for (int b = 0; b < NC; ++b) {
+        hOffU[b] = off[b] * nq;
+        hOffW[b] = off[b] * (nq + 1);
+        const double tau = grp[colg[b]].tau;
+        // node times: forward e^{-iH tau x_q}, backward e^{+iH tau (1-x_q)} and the full step
+        for (int q = 0; q < nq; ++q) {
+            hF[(size_t)b * nq + q] = tau * xq[q];
+            hB[(size_t)b * (nq + 1) + q] = -tau * (1.0 - xq[q]);
+        }
+        hB[(size_t)b * (nq + 1) + nq] = -tau;
+    }
+    if (rc == KG_OK && NC > 0 &&
+        (cudaMemcpyAsync(tauF, hF.data(), sizeof(double) * hF.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(tauB, hB.data(), sizeof(double) * hB.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(offU, hOffU.data(), sizeof(size_t) * NC, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(offW, hOffW.data(), sizeof(size_t) * NC, cudaMemcpyHostToDevice, st) != cudaSuccess))
+        rc = KG_ECUDA;
+    for (int b = 0; rc == KG_OK && b < NC; ++b) {
+        const Group& G = grp[colg[b]];
+        rc = launch_cop(s, G.nb, orb[2 * G.idx[b - G.col0]], G.spin, G.dagger, s->gs, chi + off[b], st);
+    }
+    // ---- forward pass: checkpoints and the overlaps (for dL/dE0)
+    if (rc == KG_OK && NC > 0) rc = krylov_alloc(KF, cols, o->M, s->nsm, o->schedule);
+    if (rc == KG_OK && NC > 0) rc = krylov_alloc(KB, cols, o->M, s->nsm, o->schedule);
+    auto load = [&](Krylov& K, const double2* src) -> int {
+        for (int b = 0; b < NC; ++b)
+            KG_CUDA(cudaMemcpyAsync(K.vec(b, 0), src + off[b], sizeof(double2) * K.dim(b), cudaMemcpyDeviceToDevice,
+                                    st));
+        return KG_OK;
+    };
+    auto save = [&](Krylov& K, double2* dst) -> int {
+        for (int b = 0; b < NC; ++b)
+            KG_CUDA(cudaMemcpyAsync(dst + off[b], K.vec(b, 0), sizeof(double2) * K.dim(b), cudaMemcpyDeviceToDevice,
+                                    st));
+        return KG_OK;
+    };
+    if (rc == KG_OK && NC > 0) {
+        for (int b = 0; b < NC; ++b) {
+            const int g = colg[b], a = b - grp[g].col0;
+            ColDesc& D = KF.hdesc[b];
+            D.tau = grp[g].tau;
+            D.ov = chi + gcol(g);
+            D.n_ov = grp[g].na;
+            D.ov_stride = grp[g].dn;
+            D.ov_out = ov + ovoff[g] + (size_t)a * rows * grp[g].na;
+            D.ov_rows = rows;
+            KB.hdesc[b].tau = -grp[g].tau;
+        }
+        rc = krylov_upload(KF, st);
+        if (rc == KG_OK) rc = krylov_upload(KB, st);
+        for (int g = 0; rc == KG_OK && g < (int)grp.size(); ++g)
+            rc = launch_inner_lib(chi + gcol(g), grp[g].na, chi + gcol(g), grp[g].na, grp[g].dn, ov + ovoff[g],
+                                  rows * grp[g].na, st);
+        if (rc == KG_OK) rc = launch_set_slots(KF, 1, st);
+        if (rc == KG_OK) rc = load(KF, chi);
+    }
+    if (rc == KG_OK && NC > 0) {
+        StepRunner RF;
+        rc = RF.init(KF, o->reorth, st, o->use_graphs != 0);
+        for (int k = 0; rc == KG_OK && k <= n_steps; ++k) {
+            if (k % Kc == 0) rc = save(KF, ckpt + (size_t)(k / Kc) * tot);
+            if (rc == KG_OK && k < n_steps) rc = RF.run(st);
+        }
+        RF.release();
+    }
+    std::vector<double2> hov(nov);
+    if (rc == KG_OK && NC > 0)
+        rc = cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * nov, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                     cudaStreamSynchronize(st) == cudaSuccess
+                 ? KG_OK
+                 : KG_ECUDA;
+    // dL/dE0: dp_k/dE0 = (+i t_k) p_k (particle) or (-i t_k) p_k (hole)
+    for (int g = 0; rc == KG_OK && g < (int)grp.size(); ++g) {
+        const Group& G = grp[g];
+        const int na = G.na;
+        for (int k = 0; k < rows; ++k) {
+            const std::complex<double> dp = std::complex<double>(0.0, G.dagger ? dt * k : -dt * k) * G.pk[k];
+            for (int b = 0; b < na; ++b)
                 for (int a = 0; a < na; ++a) {
-                    ColDesc& D = KF.hdesc[a];
-                    D.tau = tau;
-                    D.ov = chi;
-                    D.n_ov = na;
-                    D.ov_stride = dn;
-                    D.ov_out = ov + (size_t)a * rows * na;
-                    D.ov_rows = rows;
-                    KB.hdesc[a].tau = -tau;
+                    const double2 v = hov[ovoff[g] + ((size_t)b * rows + k) * na + a];
+                    Ebar += (std::conj(G.Gb[((size_t)k * na + a) * na + b]) * dp * std::complex<double>(v.x, v.y)).real();
                 }
-                rc = krylov_upload(KF, st);
-            }
-            if (rc == KG_OK) rc = krylov_upload(KB, st);
-            if (rc == KG_OK) rc = launch_inner_lib(chi, na, chi, na, dn, ov, rows * na, st);
-            if (rc == KG_OK) rc = launch_set_slots(KF, 1, st);
-            auto load = [&](Krylov& K, const double2* src) -> int {
-                for (int a = 0; a < na; ++a)
-                    KG_CUDA(cudaMemcpyAsync(K.vec(a, 0), src + (size_t)a * dn, sizeof(double2) * dn,
-                                            cudaMemcpyDeviceToDevice, st));
-                return KG_OK;
-            };
-            auto save = [&](Krylov& K, double2* dst) -> int {
-                for (int a = 0; a < na; ++a)
-                    KG_CUDA(cudaMemcpyAsync(dst + (size_t)a * dn, K.vec(a, 0), sizeof(double2) * dn,
-                                            cudaMemcpyDeviceToDevice, st));
-                return KG_OK;
-            };
-            if (rc == KG_OK) rc = load(KF, chi);
-            StepRunner RF;
-            if (rc == KG_OK) rc = RF.init(KF, o->reorth, st, o->use_graphs != 0);
-            for (int k = 0; rc == KG_OK && k <= n_steps; ++k) {
-                if (k % Kc == 0) rc = save(KF, ckpt + (size_t)(k / Kc) * na * dn);
-                if (rc == KG_OK && k < n_steps) rc = RF.run(st);
-            }
-            RF.release();
-            std::vector<double2> hov((size_t)na * rows * na);
-            if (rc == KG_OK)
-                rc = cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * hov.size(), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                             cudaStreamSynchronize(st) == cudaSuccess
-                         ? KG_OK
-                         : KG_ECUDA;
-            // dL/dE0: dp_k/dE0 = (+i t_k) p_k (particle) or (-i t_k) p_k (hole)
-            for (int k = 0; rc == KG_OK && k < rows; ++k) {
-                const std::complex<double> dp = std::complex<double>(0.0, dagger ? dt * k : -dt * k) * pk[k];
-                for (int b = 0; b < na; ++b)
-                    for (int a = 0; a < na; ++a) {
-                        const double2 v = hov[((size_t)b * rows + k) * na + a];
-                        Ebar += (std::conj(Gb[((size_t)k * na + a) * na + b]) * dp * std::complex<double>(v.x, v.y)).real();
-                    }
-            }
-            // ---- backward sweep, segment by segment
-            auto sources = [&](int k, double2* dst) -> int {  // dst[b] += sum_a Gbar_{ab,k} conj(p_k) chi_a
-                Coefs cf;
-                for (int b = 0; b < na; ++b)
-                    for (int a = 0; a < na; ++a) {
-                        const std::complex<double> c = Gb[((size_t)k * na + a) * na + b] * std::conj(pk[k]);
-                        cf.c[b * na + a] = make_double2(c.real(), c.imag());
-                    }
-                k_combo<<<grid_for(dn), kThreads, 0, st>>>(chi, na, dst, na, dn, cf);
-                KG_LAUNCHED();
-                return KG_OK;
-            };
-            auto bra_part = [&](int k, const double2* psi) -> int {  // y[a] += sum_b conj(Gbar_{ab,k}) p_k psi_b
-                Coefs cf;
-                for (int a = 0; a < na; ++a)
-                    for (int b = 0; b < na; ++b) {
-                        const std::complex<double> c = std::conj(Gb[((size_t)k * na + a) * na + b]) * pk[k];
-                        cf.c[a * na + b] = make_double2(c.real(), c.imag());
-                    }
-                k_combo<<<grid_for(dn), kThreads, 0, st>>>(psi, na, y, na, dn, cf);
-                KG_LAUNCHED();
-                return KG_OK;
-            };
-            if (rc == KG_OK) rc = cudaMemsetAsync(lam, 0, sizeof(double2) * na * dn, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-            if (rc == KG_OK) rc = cudaMemsetAsync(y, 0, sizeof(double2) * na * dn, st) == cudaSuccess ? KG_OK : KG_ECUDA;
-            if (rc == KG_OK) rc = sources(n_steps, lam);  // lambda_n = s_n
-            std::vector<std::complex<double>> cw(nq);
-            for (int q = 0; q < nq; ++q) cw[q] = std::complex<double>(0.0, -tau) * wq[q];
-            StepRunner RS;
-            if (rc == KG_OK) {
-                // forward recompute inside a segment: plain steps without overlaps
-                for (auto& D : KF.hdesc) {
-                    D.n_ov = 0;
-                    D.ov = nullptr;
+        }
+    }
+    // ---- backward sweep, segment by segment
+    auto sources = [&](int k, double2* dst) -> int {  // dst[b] += sum_a Gbar_{ab,k} conj(p_k) chi_a
+        for (int g = 0; g < (int)grp.size(); ++g) {
+            const Group& G = grp[g];
+            const int na = G.na;
+            Coefs cf;
+            for (int b = 0; b < na; ++b)
+                for (int a = 0; a < na; ++a) {
+                    const std::complex<double> c = G.Gb[((size_t)k * na + a) * na + b] * std::conj(G.pk[k]);
+                    cf.c[b * na + a] = make_double2(c.real(), c.imag());
                 }
-                rc = krylov_upload(KF, st);
-            }
-            if (rc == KG_OK) rc = RS.init(KF, o->reorth, st, o->use_graphs != 0);
-            // The Krylov spaces that the segment's forward steps build are
-            // kept (basis and scalars per step) when the memory is there, so
-            // that the backward sweep reads them instead of rebuilding them.
-            const int MK = KF.M + 1;
-            double2* segV = nullptr;
-            ColScalars* segC = nullptr;
-            if (rc == KG_OK &&
-                (cudaMalloc(&segV, sizeof(double2) * (size_t)Kc * na * MK * dn) != cudaSuccess ||
-                 cudaMalloc(&segC, sizeof(ColScalars) * (size_t)Kc * na) != cudaSuccess)) {
-                cudaGetLastError();
-                cudaFree(segV);
-                cudaFree(segC);
-                segV = nullptr;
-                segC = nullptr;
-            }
-            if (segV) frees.push_back(segV);
-            if (segC) frees.push_back(segC);
-            std::vector<double2*> baseV(na);
-            for (int a = 0; a < na; ++a) baseV[a] = KF.hdesc[a].V;
-            auto point_kf = [&](int step) -> int {  // step < 0: KF's own basis
-                for (int a = 0; a < na; ++a)
-                    KF.hdesc[a].V = step < 0 ? baseV[a] : segV + ((size_t)step * na + a) * MK * dn;
-                KG_TRY(krylov_upload(KF, st));
-                if (step >= 0)
-                    KG_CUDA(cudaMemcpyAsync(KF.cs, segC + (size_t)step * na, sizeof(ColScalars) * na,
-                                            cudaMemcpyDeviceToDevice, st));
-                return KG_OK;
-            };
-            for (int c = (n_steps - 1) / Kc; rc == KG_OK && c >= 0 && n_steps > 0; --c) {
-                const int k0 = c * Kc, k1 = std::min(n_steps, k0 + Kc);
-                rc = load(KF, ckpt + (size_t)c * na * dn);
-                if (rc == KG_OK) rc = save(KF, seg);
-                for (int k = k0 + 1; rc == KG_OK && k <= k1; ++k) {
-                    rc = RS.run(st);
-                    if (rc == KG_OK) rc = save(KF, seg + (size_t)(k - k0) * na * dn);
-                    if (rc == KG_OK && segV) {
-                        // basis of the step k-1 -> k: v_0 = psi_{k-1}, then V_1..V_M as built
-                        const int sidx = k - 1 - k0;
-                        for (int a = 0; rc == KG_OK && a < na; ++a) {
-                            double2* dst = segV + ((size_t)sidx * na + a) * MK * dn;
-                            if (cudaMemcpyAsync(dst, seg + (size_t)sidx * na * dn + (size_t)a * dn,
-                                                sizeof(double2) * dn, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-                                cudaMemcpyAsync(dst + dn, KF.vec(a, 1), sizeof(double2) * (size_t)(MK - 1) * dn,
-                                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                                rc = KG_ECUDA;
-                        }
-                        if (rc == KG_OK &&
-                            cudaMemcpyAsync(segC + (size_t)sidx * na, KF.cs, sizeof(ColScalars) * na,
+            k_combo<<<grid_for(G.dn), kThreads, 0, st>>>(chi + gcol(g), na, dst + gcol(g), na, G.dn, cf);
+            KG_LAUNCHED();
+        }
+        return KG_OK;
+    };
+    auto bra_part = [&](int k, const double2* psi) -> int {  // y[a] += sum_b conj(Gbar_{ab,k}) p_k psi_b
+        for (int g = 0; g < (int)grp.size(); ++g) {
+            const Group& G = grp[g];
+            const int na = G.na;
+            Coefs cf;
+            for (int a = 0; a < na; ++a)
+                for (int b = 0; b < na; ++b) {
+                    const std::complex<double> c = std::conj(G.Gb[((size_t)k * na + a) * na + b]) * G.pk[k];
+                    cf.c[a * na + b] = make_double2(c.real(), c.imag());
+                }
+            k_combo<<<grid_for(G.dn), kThreads, 0, st>>>(psi + gcol(g), na, y + gcol(g), na, G.dn, cf);
+            KG_LAUNCHED();
+        }
+        return KG_OK;
+    };
+    if (rc == KG_OK && NC > 0) rc = cudaMemsetAsync(lam, 0, sizeof(double2) * tot, st) == cudaSuccess ? KG_OK : KG_ECUDA;
+    if (rc == KG_OK && NC > 0) rc = cudaMemsetAsync(y, 0, sizeof(double2) * tot, st) == cudaSuccess ? KG_OK : KG_ECUDA;
+    if (rc == KG_OK && NC > 0) rc = sources(n_steps, lam);  // lambda_n = s_n
+    std::vector<std::vector<std::complex<double>>> cw(grp.size(), std::vector<std::complex<double>>(nq));
+    for (int g = 0; g < (int)grp.size(); ++g)
+        for (int q = 0; q < nq; ++q) cw[g][q] = std::complex<double>(0.0, -grp[g].tau) * wq[q];
+    if (rc == KG_OK && NC > 0) {
+        StepRunner RS;
+        // forward recompute inside a segment: plain steps without overlaps
+        for (auto& D : KF.hdesc) {
+            D.n_ov = 0;
+            D.ov = nullptr;
+        }
+        rc = krylov_upload(KF, st);
+        if (rc == KG_OK) rc = RS.init(KF, o->reorth, st, o->use_graphs != 0);
+        // The Krylov spaces that the segment's forward steps build are kept
+        // (basis and scalars per step) when the memory is there, so that the
+        // backward sweep reads them instead of rebuilding them.
+        const int MK = KF.M + 1;
+        double2* segV = nullptr;
+        ColScalars* segC = nullptr;
+        if (rc == KG_OK && (cudaMalloc(&segV, sizeof(double2) * (size_t)Kc * MK * tot) != cudaSuccess ||
+                            cudaMalloc(&segC, sizeof(ColScalars) * (size_t)Kc * NC) != cudaSuccess)) {
+            cudaGetLastError();
+            cudaFree(segV);
+            cudaFree(segC);
+            segV = nullptr;
+            segC = nullptr;
+        }
+        if (segV) frees.push_back(segV);
+        if (segC) frees.push_back(segC);
+        std::vector<double2*> baseV(NC);
+        for (int b = 0; b < NC; ++b) baseV[b] = KF.hdesc[b].V;
+        auto segbase = [&](int step, int b) { return segV + (size_t)step * MK * tot + (size_t)MK * off[b]; };
+        auto point_kf = [&](int step) -> int {  // step < 0: KF's own basis
+            for (int b = 0; b < NC; ++b) KF.hdesc[b].V = step < 0 ? baseV[b] : segbase(step, b);
+            KG_TRY(krylov_upload(KF, st));
+            if (step >= 0)
+                KG_CUDA(cudaMemcpyAsync(KF.cs, segC + (size_t)step * NC, sizeof(ColScalars) * NC,
+                                        cudaMemcpyDeviceToDevice, st));
+            return KG_OK;
+        };
+        for (int c = (n_steps - 1) / Kc; rc == KG_OK && c >= 0 && n_steps > 0; --c) {
+            const int k0 = c * Kc, k1 = std::min(n_steps, k0 + Kc);
+            rc = load(KF, ckpt + (size_t)c * tot);
+            if (rc == KG_OK) rc = save(KF, seg);
+            for (int k = k0 + 1; rc == KG_OK && k <= k1; ++k) {
+                rc = RS.run(st);
+                if (rc == KG_OK) rc = save(KF, seg + (size_t)(k - k0) * tot);
+                if (rc == KG_OK && segV) {
+                    // basis of the step k-1 -> k: v_0 = psi_{k-1}, then V_1..V_M as built
+                    const int sidx = k - 1 - k0;
+                    for (int b = 0; rc == KG_OK && b < NC; ++b) {
+                        const int db = KF.dim(b);
+                        double2* dst = segbase(sidx, b);
+                        if (cudaMemcpyAsync(dst, seg + (size_t)sidx * tot + off[b], sizeof(double2) * db,
+                                            cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                            cudaMemcpyAsync(dst + db, KF.vec(b, 1), sizeof(double2) * (size_t)(MK - 1) * db,
                                             cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                             rc = KG_ECUDA;
                     }
-                }
-                for (int k = k1; rc == KG_OK && k > k0; --k) {
-                    rc = bra_part(k, seg + (size_t)(k - k0) * na * dn);
-                    // forward space of psi_{k-1}: node vectors u_q
-                    if (segV) {
-                        if (rc == KG_OK) rc = point_kf(k - 1 - k0);
-                    } else {
-                        if (rc == KG_OK) rc = load(KF, seg + (size_t)(k - 1 - k0) * na * dn);
-                        if (rc == KG_OK) rc = build_space(KF, o->reorth, st);
-                    }
-                    if (rc == KG_OK) rc = launch_tridiag_multi(KF, tauF, nq, cqF, st);
-                    if (rc == KG_OK) {
-                        k_lincomb<<<dim3(grid_for(dn), na), kThreads, 0, st>>>(KF.desc, KF.cs, KF.M, cqF, nq, Uq);
-                        KG_LAUNCHED();
-                    }
-                    // backward space of lambda_k: node vectors w_q and U^dag lambda_k
-                    if (rc == KG_OK) rc = load(KB, lam);
-                    if (rc == KG_OK) rc = build_space(KB, o->reorth, st);
-                    if (rc == KG_OK) rc = launch_tridiag_multi(KB, tauB, nq + 1, cqB, st);
-                    if (rc == KG_OK) {
-                        k_lincomb<<<dim3(grid_for(dn), na), kThreads, 0, st>>>(KB.desc, KB.cs, KB.M, cqB, nq + 1, Wq);
-                        KG_LAUNCHED();
-                    }
-                    for (int b = 0; rc == KG_OK && b < na; ++b)
-                        rc = grad_pass(nb, Uq + (size_t)b * nq * dn, Wq + (size_t)b * (nq + 1) * dn, cw, dmap, P,
-                                       partial, nblk, g, st);
-                    // lambda_{k-1} = U^dag lambda_k + s_{k-1}
-                    for (int b = 0; rc == KG_OK && b < na; ++b)
-                        rc = cudaMemcpyAsync(lam + (size_t)b * dn, Wq + ((size_t)b * (nq + 1) + nq) * dn,
-                                             sizeof(double2) * dn, cudaMemcpyDeviceToDevice, st) == cudaSuccess
-                                 ? KG_OK
-                                 : KG_ECUDA;
-                    if (rc == KG_OK) rc = sources(k - 1, lam);
-                }
-                if (rc == KG_OK && segV) rc = point_kf(-1);  // the step graph reads KF's own basis
-            }
-            RS.release();
-            if (rc == KG_OK) rc = bra_part(0, chi);
-            // z += c_op^dag applied to lambda_0 and to y (back to the N sector)
-            for (int a = 0; rc == KG_OK && a < na; ++a) {
-                const int site = orb[2 * idx[spin][a]];
-                for (int which = 0; rc == KG_OK && which < 2; ++which) {
-                    const double2* v = (which == 0 ? lam : y) + (size_t)a * dn;
-                    rc = launch_cop(nb, s, site, spin, dagger ? 0 : 1, v, tmp, st);
-                    if (rc == KG_OK) rc = axpby(1.0, tmp, 1.0, z, d0, st);
+                    if (rc == KG_OK && cudaMemcpyAsync(segC + (size_t)sidx * NC, KF.cs, sizeof(ColScalars) * NC,
+                                                       cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                        rc = KG_ECUDA;
                 }
             }
-            // propagation states are checked for NaN/Inf by the Lanczos kernels
-            if (rc == KG_OK) {
-                std::vector<ColScalars> h(na);
-                if (cudaMemcpy(h.data(), KB.cs, sizeof(ColScalars) * na, cudaMemcpyDeviceToHost) != cudaSuccess)
-                    rc = KG_ECUDA;
-                for (auto& c : h)
-                    if (rc == KG_OK && c.status == KG_ENUMERIC) {
-                        set_error("non-finite value in the adjoint sweep");
-                        rc = KG_ENUMERIC;
-                    }
+            for (int k = k1; rc == KG_OK && k > k0; --k) {
+                rc = bra_part(k, seg + (size_t)(k - k0) * tot);
+                // forward space of psi_{k-1}: node vectors u_q
+                if (segV) {
+                    if (rc == KG_OK) rc = point_kf(k - 1 - k0);
+                } else {
+                    if (rc == KG_OK) rc = load(KF, seg + (size_t)(k - 1 - k0) * tot);
+                    if (rc == KG_OK) rc = build_space(KF, o->reorth, st);
+                }
+                if (rc == KG_OK) rc = launch_tridiag_multi(KF, tauF, nq, cqF, st);
+                if (rc == KG_OK) {
+                    k_lincomb<<<dim3(grid_for((int)(tot / NC) + 1), NC), kThreads, 0, st>>>(KF.desc, KF.cs, KF.M, cqF,
+                                                                                         nq, Uq, offU);
+                    KG_LAUNCHED();
+                }
+                // backward space of lambda_k: node vectors w_q and U^dag lambda_k
+                if (rc == KG_OK) rc = load(KB, lam);
+                if (rc == KG_OK) rc = build_space(KB, o->reorth, st);
+                if (rc == KG_OK) rc = launch_tridiag_multi(KB, tauB, nq + 1, cqB, st);
+                if (rc == KG_OK) {
+                    k_lincomb<<<dim3(grid_for((int)(tot / NC) + 1), NC), kThreads, 0, st>>>(KB.desc, KB.cs, KB.M, cqB,
+                                                                                         nq + 1, Wq, offW);
+                    KG_LAUNCHED();
+                }
+                for (int b = 0; rc == KG_OK && b < NC; ++b)
+                    rc = grad_pass(grp[colg[b]].nb, Uq + hOffU[b], Wq + hOffW[b], cw[colg[b]], dmap, P, partial, nblk,
+                                   g, st);
+                // lambda_{k-1} = U^dag lambda_k + s_{k-1}
+                for (int b = 0; rc == KG_OK && b < NC; ++b)
+                    rc = cudaMemcpyAsync(lam + off[b], Wq + hOffW[b] + (size_t)nq * KB.dim(b),
+                                         sizeof(double2) * KB.dim(b), cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                             ? KG_OK
+                             : KG_ECUDA;
+                if (rc == KG_OK) rc = sources(k - 1, lam);
             }
-            krylov_free(KF);
-            krylov_free(KB);
+            if (rc == KG_OK && segV) rc = point_kf(-1);  // the step graph reads KF's own basis
         }
+        RS.release();
+    }
+    if (rc == KG_OK && NC > 0) rc = bra_part(0, chi);
+    // z += c_op^dag applied to lambda_0 and to y (back to the N sector)
+    for (int b = 0; rc == KG_OK && b < NC; ++b) {
+        const Group& G = grp[colg[b]];
+        const int site = orb[2 * G.idx[b - G.col0]];
+        for (int which = 0; rc == KG_OK && which < 2; ++which) {
+            const double2* v = (which == 0 ? lam : y) + off[b];
+            rc = launch_cop(G.nb, s, site, G.spin, G.dagger ? 0 : 1, v, tmp, st);
+            if (rc == KG_OK) rc = axpby(1.0, tmp, 1.0, z, d0, st);
+        }
+    }
+    // propagation states are checked for NaN/Inf by the Lanczos kernels
+    if (rc == KG_OK && NC > 0) {
+        std::vector<ColScalars> h(NC);
+        if (cudaMemcpy(h.data(), KB.cs, sizeof(ColScalars) * NC, cudaMemcpyDeviceToHost) != cudaSuccess) rc = KG_ECUDA;
+        for (auto& c : h)
+            if (rc == KG_OK && c.status == KG_ENUMERIC) {
+                set_error("non-finite value in the adjoint sweep");
+                rc = KG_ENUMERIC;
+            }
+    }
+    if (NC > 0) {
+        krylov_free(KF);
+        krylov_free(KB);
     }
     // ---- ground-state terms in the N sector
     double2* x = nullptr;
