@@ -464,8 +464,19 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         float cx = 0.f, cy = 0.f;
         int q = 0;
         if (V32) {
-            // four loads in flight before their terms are applied
-            for (; q + 4 <= m32; q += 4) {
+            // eight loads in flight before their terms are applied
+            for (; q + 8 <= m32; q += 8) {
+                float2 v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = V32[(size_t)idx32[q + r] * d + i];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const float2 c = coef32[q + r];
+                    cx = fmaf(c.x, v[r].x, fmaf(-c.y, v[r].y, cx));
+                    cy = fmaf(c.x, v[r].y, fmaf(c.y, v[r].x, cy));
+                }
+            }
+            if (q + 4 <= m32) {
                 float2 v[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) v[r] = V32[(size_t)idx32[q + r] * d + i];
@@ -475,6 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
                     cx = fmaf(c.x, v[r].x, fmaf(-c.y, v[r].y, cx));
                     cy = fmaf(c.x, v[r].y, fmaf(c.y, v[r].x, cy));
                 }
+                q += 4;
             }
             for (; q < m32; ++q) {
                 const float2 v = V32[(size_t)idx32[q] * d + i], c = coef32[q];
