@@ -758,6 +758,7 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
 // FP64 instruction serves the whole vector -- the eigen-decomposition's
 // bulge chase is serial.  Modes 0 and 2 as in k_tridiag.
 constexpr int kTaylorTerms = 18;
+constexpr int kMaxTaus = 32;  // times per column in one mode-2 launch
 
 template <int R>
 __device__ __forceinline__ void tri_apply(const double (&a)[R], const double (&bl)[R], const double (&br)[R],
@@ -810,13 +811,36 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_texp(const ColDesc* desc, Co
     for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
     const double beta0 = C->beta0;
     const int nt = mode == 0 ? 1 : ntau;
-    for (int t = 0; t < nt; ++t) {
-        const double tau = mode == 0 ? desc[b].tau : taus[(size_t)b * ntau + t];
+    // Several times of one sign (mode 2: quadrature nodes) are taken in order
+    // of |tau|, each from the previous result: e^{-iT t_n} e_1 =
+    // e^{-iT (t_n - t_{n-1})} e^{-iT t_{n-1}} e_1.  Times of mixed signs
+    // restart from e_1.
+    int order[kMaxTaus];
+    for (int t = 0; t < nt; ++t) order[t] = t;
+    if (mode == 2)
+        for (int a1 = 1; a1 < nt; ++a1)  // insertion sort by |tau| (nt <= kMaxTaus)
+            for (int a2 = a1; a2 > 0 && fabs(taus[(size_t)b * ntau + order[a2]]) <
+                                            fabs(taus[(size_t)b * ntau + order[a2 - 1]]); --a2) {
+                const int tmp = order[a2];
+                order[a2] = order[a2 - 1];
+                order[a2 - 1] = tmp;
+            }
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = make_double2((lane + 32 * r) == 0 ? 1.0 : 0.0, 0.0);
+    double tprev = 0.0;
+    for (int tt = 0; tt < nt; ++tt) {
+        const int t = order[tt];
+        const double tfull = mode == 0 ? desc[b].tau : taus[(size_t)b * ntau + t];
+        if (tfull * tprev < 0.0) {  // sign change: start again from e_1
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = make_double2((lane + 32 * r) == 0 ? 1.0 : 0.0, 0.0);
+            tprev = 0.0;
+        }
+        const double tau = tfull - tprev;
+        tprev = tfull;
         const int nsub = max(1, (int)ceil(2.0 * g * fabs(tau)));
         const double h = tau / nsub;
-        double2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = make_double2((lane + 32 * r) == 0 ? 1.0 : 0.0, 0.0);
         for (int sub = 0; sub < nsub; ++sub) {
             double2 term[R], sum[R], y[R];
 #pragma unroll
@@ -1051,6 +1075,10 @@ __global__ void __launch_bounds__(kThreads) k_rq(const double2* x, const double2
 // Coefficients of exp(-i H t) v_0 for ntau times per column (taus[b][t]),
 // into cq[b][t][0..M) (already times the scales of the stored vectors).
 int launch_tridiag_multi(Krylov& K, const double* taus, int ntau, double2* cq, cudaStream_t st) {
+    if (ntau < 1 || ntau > kMaxTaus) {
+        set_error("between 1 and %d times per column", kMaxTaus);
+        return KG_EINVAL;
+    }
     const int nb = (K.B + kTriWarps - 1) / kTriWarps;
     ProfScope ps("tridiag", st);
     if (!(K.schedule & 2)) return launch_texp(K, 2, taus, ntau, cq, st);
