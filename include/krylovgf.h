@@ -118,7 +118,10 @@ int kg_sector_strings(const kg_sector* s, unsigned int* up_host, unsigned int* d
  * hopping by bit flips with popcount fermion signs, diagonal eps and U).
  * x_dev, y_dev: complex vectors of dimension d, must not overlap.
  * stream: cudaStream_t; NULL means CUDA's legacy default stream.
- * Asynchronous (stream-ordered). */
+ * Asynchronous (stream-ordered).  When all hops of the sector share one
+ * amplitude, the hop sums are exact 64-bit integer sums of a fixed-point
+ * image of x, held in 16 d bytes of stream-ordered scratch (cudaMallocAsync
+ * from the device's default pool, freed on the same stream). */
 int kg_hpsi(kg_sector* s, const double* x_dev, double* y_dev, void* stream);
 
 /* ---- c / c^dag sector maps ------------------------------------------

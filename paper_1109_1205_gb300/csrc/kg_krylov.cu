@@ -96,7 +96,15 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         D.pad = 0;
         np += (size_t)D.nblk_max * kPart;
     }
-    KG_CUDA(cudaMalloc(&K.Vbuf, sizeof(double2) * nv));
+    // on any failure the workspace is released whole (krylov_free skips null)
+    auto need = [&](cudaError_t e, const char* what) -> int {
+        if (e == cudaSuccess) return KG_OK;
+        cudaGetLastError();
+        krylov_free(K);
+        set_error("Krylov workspace: %s failed (%s)", what, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? KG_ENOMEM : KG_ECUDA;
+    };
+    KG_TRY(need(cudaMalloc(&K.Vbuf, sizeof(double2) * nv), "basis allocation"));
     // Planes read by the Gram-Schmidt kernels (Re+Im for the three-multiply
     // dot products, a truncated FP32 copy for the small correction terms).
     // They are optional: without the memory the kernels use V alone.
@@ -105,20 +113,19 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         cudaGetLastError();
         cudaFree(K.Sbuf);
         cudaFree(K.V32buf);
-    cudaFree(K.Xfbuf);
         K.Sbuf = nullptr;
         K.V32buf = nullptr;
     }
-    KG_CUDA(cudaMalloc(&K.Wbuf, sizeof(double2) * 2 * nw));
-    if (nx) KG_CUDA(cudaMalloc(&K.Xfbuf, sizeof(longlong2) * nx));
-    KG_CUDA(cudaMalloc(&K.partbuf, sizeof(double) * np));
-    KG_CUDA(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B));
-    KG_CUDA(cudaMalloc(&K.secs, sizeof(SecView) * K.B));
-    KG_CUDA(cudaMalloc(&K.cs, sizeof(ColScalars) * K.B));
-    KG_CUDA(cudaMalloc(&K.cnt, sizeof(unsigned) * K.B));
-    KG_CUDA(cudaMalloc(&K.Q, sizeof(double) * (size_t)K.B * M * M));
-    KG_CUDA(cudaMemset(K.cs, 0, sizeof(ColScalars) * K.B));
-    KG_CUDA(cudaMemset(K.cnt, 0, sizeof(unsigned) * K.B));
+    KG_TRY(need(cudaMalloc(&K.Wbuf, sizeof(double2) * 2 * nw), "work vector allocation"));
+    if (nx) KG_TRY(need(cudaMalloc(&K.Xfbuf, sizeof(longlong2) * nx), "fixed-point image allocation"));
+    KG_TRY(need(cudaMalloc(&K.partbuf, sizeof(double) * np), "partial-sum allocation"));
+    KG_TRY(need(cudaMalloc(&K.desc, sizeof(ColDesc) * K.B), "descriptor allocation"));
+    KG_TRY(need(cudaMalloc(&K.secs, sizeof(SecView) * K.B), "sector view allocation"));
+    KG_TRY(need(cudaMalloc(&K.cs, sizeof(ColScalars) * K.B), "scalar allocation"));
+    KG_TRY(need(cudaMalloc(&K.cnt, sizeof(unsigned) * K.B), "ticket allocation"));
+    KG_TRY(need(cudaMalloc(&K.Q, sizeof(double) * (size_t)K.B * M * M), "eigenvector allocation"));
+    KG_TRY(need(cudaMemset(K.cs, 0, sizeof(ColScalars) * K.B), "scalar reset"));
+    KG_TRY(need(cudaMemset(K.cnt, 0, sizeof(unsigned) * K.B), "ticket reset"));
     size_t ov = 0, ow = 0, op = 0, ox = 0;
     for (int b = 0; b < K.B; ++b) {
         ColDesc& D = K.hdesc[b];
@@ -138,8 +145,8 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         ow += (size_t)D.d;
         op += (size_t)D.nblk_max * kPart;
     }
-    KG_CUDA(cudaMemcpy(K.secs, K.hsec.data(), sizeof(SecView) * K.B, cudaMemcpyHostToDevice));
-    KG_CUDA(cudaMemcpy(K.desc, K.hdesc.data(), sizeof(ColDesc) * K.B, cudaMemcpyHostToDevice));
+    KG_TRY(need(cudaMemcpy(K.secs, K.hsec.data(), sizeof(SecView) * K.B, cudaMemcpyHostToDevice), "upload"));
+    KG_TRY(need(cudaMemcpy(K.desc, K.hdesc.data(), sizeof(ColDesc) * K.B, cudaMemcpyHostToDevice), "upload"));
     return KG_OK;
 }
 
