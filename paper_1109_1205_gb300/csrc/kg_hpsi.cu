@@ -278,7 +278,6 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
     double *sm = sh.sm, *bs = sh.bs, *red = sh.red;
     int* smi = sh.smi;
     if (j >= C->m_eff) return;
-    __syncthreads();  // the previous item (round lists) is done with S and amp
     if (threadIdx.x == 0) S = *D.sec;
     __syncthreads();
     stage_amplitudes(S, amp);
