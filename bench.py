@@ -296,10 +296,11 @@ def run_ours(args):
         cpu = cpu_baseline_sample(args.cpu_seconds)
 
     # ---- the batched and adjoint forms against the plain GPU path
-    batched = adjoint = None
+    batched = adjoint = spectral = None
     if rank == 0 and world == 1 and not args.no_extras:
         batched = batched_vs_plain(args.batch_instances, args.batch_steps)
         adjoint = adjoint_vs_fd()
+        spectral = lanczos_spectral(si, opts)
 
     if rank == 0:
         clocks = clk.summary()
@@ -315,7 +316,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "hpsi": hpsi,
             "fp64_tflops_measured": round(fp64, 3), "cpu_baseline": cpu, "clocks": clocks,
             "setup_s": round(t_setup, 2), "E0_ini": E0, "gs_resid": res,
-            "batched": batched, "adjoint": adjoint,
+            "batched": batched, "adjoint": adjoint, "spectral": spectral,
         }
         print(json.dumps(line))
     if world > 1:
@@ -381,6 +382,29 @@ def batched_vs_plain(n_inst, n_steps):
             "batched_value": round(gsteps / tb, 1), "plain_value": round(gsteps / tp, 1),
             "batched_s": round(tb, 3), "plain_s": round(tp, 3), "speedup": round(tp / tb, 2),
             "max_abs_diff": err}
+
+
+def lanczos_spectral(si, opts, n=100):
+    """The conventional Lanczos Green's function (frequency domain) of the
+    U = 8 ring's ground state: n = 100 Lanczos steps from c^dag_0|0> and
+    c_0|0> (two columns, d = 731,808), continued fractions on 2001
+    frequencies.  Ground state already computed (untimed)."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    omega = np.linspace(-10.0, 10.0, 2001)
+    kg.kg_green_lanczos(si.handle, [(0, 0)], 8, omega[:3], 0.1, opts)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gg, Gl, coef = kg.kg_green_lanczos(si.handle, [(0, 0)], n, omega, 0.1, opts)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    A = -(Gg[0] + Gl[0]).imag / np.pi
+    return {"workload": "Lanczos G(omega) of the c2 ring ground state (U=8): n=%d steps from c^dag_0|0> and c_0|0> "
+                        "(d=731808 each), eta=0.1, 2001 frequencies" % n,
+            "seconds": round(t, 3), "lanczos_steps_per_s": round(2 * n / t, 1),
+            "spectral_weight": round(float(np.trapezoid(A, omega) if hasattr(np, "trapezoid") else np.trapz(A, omega)), 4)}
 
 
 def adjoint_vs_fd():

@@ -197,6 +197,26 @@ int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_o
 int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps,
                          const kg_opts* o, double* G_gtr, double* G_les);
 
+/* ---- conventional Lanczos Green's function (frequency domain) ----------
+ * Section 2, Eqs. (gomega), (resolv) and (gapprox): for each diagonal orbital
+ * alpha = (site, spin), an n-step Lanczos run (full reorthogonalisation) from
+ * c^dag_alpha |0> gives the n-pole particle part and one from c_alpha |0> the
+ * hole part, evaluated as continued fractions in the Lanczos coefficients:
+ *   G_gtr[a][w] = <0| c_a (omega_w + i eta - H + E0)^{-1} c^dag_a |0>,
+ *   G_les[a][w] = <0| c^dag_a (omega_w + i eta + H - E0)^{-1} c_a |0>,
+ * so that G_gtr + G_les is the retarded function of Eq. (gomega) with the
+ * broadening eta, and A(w) = -Im(G_gtr + G_les)/pi the spectral function.
+ * Runs kg_ground_state first if needed.
+ *   orb: host int[2 n_orb] (site, spin) pairs; 1 <= n <= 255; eta >= 0.
+ *   omega: host double[n_omega]; G_gtr, G_les: host complex [n_orb][n_omega].
+ *   coef: host double[n_orb][2][2n] or NULL -- for each orbital, the particle
+ *     (index 0) and hole (1) coefficients a_0..a_{n-1}, b_0..b_{n-1}
+ *     (b_0 the norm of the start vector, b_j coupling j-1 and j), zero beyond
+ *     the Krylov dimension reached.
+ * A part whose neighbour sector does not exist (full or empty band) is zero. */
+int kg_green_lanczos(kg_sector* s, const int* orb, int n_orb, int n, const double* omega, int n_omega,
+                     double eta, const kg_opts* o, double* G_gtr, double* G_les, double* coef);
+
 /* ---- batched equilibrium Green's functions ----------------------------
  * The equilibrium Green's functions of n_inst independent sectors (for
  * example the repeated impurity solves of DMFT/VCA-type embedding schemes,

@@ -206,6 +206,71 @@ def green_equilibrium(model, orbitals, dt, n_steps, gs=None, K=80, tol=1e-12):
     return G_gtr, G_les, E0
 
 
+def lanczos_run(sector, v0, n):
+    """n steps of the Lanczos recursion of Eq. (recursion) from v0 with full
+    reorthogonalisation (modified Gram-Schmidt, twice, against every stored
+    vector).  Returns (a, b, norm0): the diagonal a_0..a_{m-1}, the couplings
+    b_1..b_{m-1} (b[j-1] couples vectors j-1 and j) and ||v0||; m <= n is
+    smaller after an invariant subspace is reached."""
+    norm0 = float(np.linalg.norm(v0))
+    a, b = [], []
+    if norm0 == 0.0:
+        return np.zeros(0), np.zeros(0), 0.0
+    V = [v0 / norm0]
+    for j in range(n):
+        w = sector.hpsi(V[j])
+        if j > 0:
+            w = w - b[-1] * V[j - 1]
+        aj = float(np.vdot(V[j], w).real)
+        w = w - aj * V[j]
+        for _ in range(2):
+            for v in V:
+                w = w - np.vdot(v, w) * v
+        a.append(aj)
+        if j + 1 == n:
+            break
+        bj = float(np.linalg.norm(w))
+        if bj <= 1e-12 * (abs(aj) + (b[-1] if b else 0.0)):
+            break
+        b.append(bj)
+        V.append(w / bj)
+    return np.array(a), np.array(b), norm0
+
+
+def green_lanczos(model, orbitals, n, omega, eta, gs=None, K=80, tol=1e-12):
+    """The Lanczos Green's function of Eq. (gapprox) for diagonal orbitals:
+    a second Lanczos run of n steps from c^dag_a|0> (particle part) or c_a|0>
+    (hole part), its Ritz pairs (E_m, |m>) from the tridiagonal matrix
+    (Eq. (eigen)), and the n-pole sum
+        G^>_a(w) = sum_m |<m|c^dag_a 0>|^2 / (w + i eta - E_m + E0),
+        G^<_a(w) = sum_m |<m|c_a 0>|^2 / (w + i eta + E_m - E0),
+    with <m|c^dag_a 0> = ||c^dag_a 0|| (Q)_{0m}.  Returns (G_gtr, G_les, E0),
+    each G of shape [n_orb, len(omega)]."""
+    sec = Sector(model)
+    E0, psi0, _ = sec.ground_state(K=K, tol=tol) if gs is None else gs
+    omega = np.asarray(omega, dtype=np.float64)
+    G_gtr = np.zeros((len(orbitals), omega.size), dtype=np.complex128)
+    G_les = np.zeros_like(G_gtr)
+    for i, (site, spin) in enumerate(orbitals):
+        for dagger, G in ((True, G_gtr), (False, G_les)):
+            nb = sec.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            v0 = sec.apply_cop(nb, site, spin, dagger, psi0)
+            a, b, norm0 = lanczos_run(nb, v0, n)
+            if norm0 == 0.0:
+                continue
+            T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+            Em, Q = np.linalg.eigh(T)
+            wgt = (norm0 * Q[0, :]) ** 2
+            for m in range(len(Em)):
+                if dagger:
+                    G[i] += wgt[m] / (omega + 1j * eta - Em[m] + E0)
+                else:
+                    G[i] += wgt[m] / (omega + 1j * eta + Em[m] - E0)
+    return G_gtr, G_les, E0
+
+
 def keldysh_vectors(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):
     """Steps (i)-(iii) of Section 4: returns (E0, Phi, Psi, Chi).
 

@@ -66,6 +66,7 @@ _sig = {
     "kg_green_keldysh": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_equilibrium_batched": (_I, [_P, _I, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_green_equilibrium_vjp": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _I, _P, _P, _P, _P, _P, _P]),
+    "kg_green_lanczos": (_I, [_P, _P, _I, _I, _P, _I, _D, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -244,6 +245,23 @@ def kg_green_equilibrium_vjp(handle, L, orbitals, dt, n_steps, dG_gtr=None, dG_l
     return g_eps, g_hre, g_him, g_U
 
 
+def kg_green_lanczos(handle, orbitals, n, omega, eta, opts=None):
+    """Lanczos (continued-fraction) Green's function of the diagonal orbitals:
+    returns (G_gtr, G_les, coef) with G of shape [n_orb, n_omega] (complex) and
+    coef [n_orb, 2, 2n] (particle / hole; a_0..a_{n-1}, b_0..b_{n-1})."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n_orb = orb.shape[0]
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).ravel())
+    Gg = np.zeros((n_orb, w.size), dtype=np.complex128)
+    Gl = np.zeros_like(Gg)
+    coef = np.zeros((n_orb, 2, 2 * n), dtype=np.float64)
+    _check(lib.kg_green_lanczos(handle, orb.ctypes.data, n_orb, int(n), w.ctypes.data if w.size else None, w.size,
+                                float(eta), ctypes.byref(o), Gg.ctypes.data, Gl.ctypes.data, coef.ctypes.data),
+           "kg_green_lanczos")
+    return Gg, Gl, coef
+
+
 def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):
     o = opts if opts is not None else kg_opts_default()
     orb = _orb_array(orbitals)
@@ -372,6 +390,9 @@ class Sector:
 
     def green_equilibrium(self, orbitals, dt, n_steps, opts=None):
         return kg_green_equilibrium(self.handle, orbitals, dt, n_steps, opts)
+
+    def green_lanczos(self, orbitals, n, omega, eta, opts=None):
+        return kg_green_lanczos(self.handle, orbitals, n, omega, eta, opts)
 
 
 class Keldysh:

@@ -305,7 +305,7 @@ static int grad_pass(const kg_sector* sec, const double2* U, const double2* Wv, 
 
 // Lanczos space of every column's V_0 without the final combination (the
 // caller forms the vectors it needs at the times it needs).
-static int build_space(Krylov& K, int reorth, cudaStream_t st) {
+int build_space(Krylov& K, int reorth, cudaStream_t st) {
     KG_TRY(launch_colnorm(K, st));
     for (int j = 0; j < K.M; ++j) {
         KG_TRY(launch_lanczos_hpsi(K, j, st));

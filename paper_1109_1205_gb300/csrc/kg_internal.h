@@ -213,6 +213,9 @@ int launch_colnorm(Krylov& K, cudaStream_t st);
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st);
 // Lanczos update: V_{j+1} = w - a_j v_j - sum_k h_k v_k (or in place for the
 // second pass), then b_{j+1} = ||V_{j+1}||, scale, breakdown test.
+// The Lanczos space (colnorm, then M iterations of H*psi, Gram-Schmidt and
+// update) of every column's V_0, without the combination step.
+int build_space(Krylov& K, int reorth, cudaStream_t st);
 // level: the reorthogonalisation level (0, 1, 2); second: the second pass.
 // diag[s] = e_up[i_up] + e_dn[i_dn] + sum of U over doubly occupied sites.
 int launch_diag_table(const SecView& S, double* diag, cudaStream_t st);

@@ -77,5 +77,6 @@ def test_argument_validation_before_device_use(kg):
     assert lib.kg_hpsi(None, None, None, None) == kg.KG_EINVAL
     assert lib.kg_ground_state(None, None, None, None, None) == kg.KG_EINVAL
     assert lib.kg_keldysh_row(None, 0, None, None) == kg.KG_EINVAL
+    assert lib.kg_green_lanczos(None, None, 0, 0, None, 0, 0.0, None, None, None, None) == kg.KG_EINVAL
     lib.kg_free_sector(None)
     lib.kg_keldysh_free(None)

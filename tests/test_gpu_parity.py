@@ -442,3 +442,55 @@ def test_c2_full_size_sampled():
         # half filling + particle-hole symmetry of the ring: n_i(t) = 1/2
         assert np.max(np.abs((-1j * np.diag(dl)).real - 0.5)) < 1e-10
     K.close()
+
+
+# ------------------------------------- Lanczos G(omega), Eq. (gapprox)
+@pytest.mark.parametrize("name", ["star_c1", "chain_int", "complex"])
+def test_green_lanczos_parity(name):
+    """Continued fractions of the GPU Lanczos coefficients against the oracle's
+    Ritz-pair sum (Eq. (gapprox)) from its own Lanczos runs.  Past the first
+    converged Ritz values the individual coefficients of two correct Lanczos
+    runs part at rounding level times a large condition number, and so does
+    an unconverged n-pole function; the comparison is therefore made where
+    the result is defined to rounding: Krylov spaces that exhaust the sector
+    (the resolvent is then exact)."""
+    if name == "star_c1":
+        m, orbs, n = W.config_c1()["model"], [(0, 0), (2, 1)], 40   # the Krylov space closes at ~13
+    elif name == "chain_int":
+        # uniform hopping: exact integer hop sums; sectors of 100 and 50 states
+        m, orbs, n = W.siam_chain(5, 3.0, 2, 3, field=0.7), [(0, 0), (3, 1)], 120
+    else:
+        m, orbs, n = W.random_model(5, 2, 2, seed=23, complex_hopping=True), [(1, 0), (4, 1)], 120
+    omega = np.linspace(-8.0, 8.0, 41)
+    s = kg.Sector(m)
+    Gg, Gl, coef = s.green_lanczos(orbs, n, omega, 0.1)
+    rg, rl, _ = oracle.green_lanczos(m, orbs, n, omega, 0.1)
+    assert np.max(np.abs(Gg - rg)) < G_TOL and np.max(np.abs(Gl - rl)) < G_TOL
+    # spectral sum rule: b_0^2 of both parts add up to <{c, c^dag}> = 1
+    assert np.max(np.abs(coef[:, 0, n] ** 2 + coef[:, 1, n] ** 2 - 1.0)) < 1e-12
+
+
+def test_green_lanczos_first_coefficients_full_size_chain():
+    """On a large sector (d = 15,876) the first Lanczos coefficients, before
+    any Ritz value converges, agree with the oracle's to rounding."""
+    m = W.siam_chain(9, 3.0, 4, 5, field=0.7)
+    s = kg.Sector(m)
+    _, _, coef = s.green_lanczos([(0, 0)], 8, np.zeros(1), 0.1)
+    sec = oracle.Sector(m)
+    _, psi0, _ = sec.ground_state(K=80, tol=1e-13)
+    nb = sec.neighbour(0, True)
+    a, b, n0 = oracle.lanczos_run(nb, sec.apply_cop(nb, 0, 0, True, psi0), 8)
+    assert np.max(np.abs(coef[0, 0, :8] - a)) < 1e-9
+    assert abs(coef[0, 0, 8] - n0) < 1e-12 and np.max(np.abs(coef[0, 0, 9:16] - b)) < 1e-9
+
+
+def test_green_lanczos_edges():
+    # full up band: no particle part for spin up; n = 1 is a single pole
+    m = W.make_model(3, 3, 1, W.chain_hopping(3), None, [2.0, 1.0, 0.5])
+    s = kg.Sector(m)
+    omega = np.linspace(-3, 3, 7)
+    Gg, Gl, coef = s.green_lanczos([(0, 0), (1, 1)], 1, omega, 0.2)
+    rg, rl, _ = oracle.green_lanczos(m, [(0, 0), (1, 1)], 1, omega, 0.2)
+    assert np.all(Gg[0] == 0) and np.max(np.abs(Gl - rl)) < G_TOL and np.max(np.abs(Gg - rg)) < G_TOL
+    with pytest.raises(kg.KGError):
+        s.green_lanczos([(0, 0)], 256, omega, 0.1)

@@ -401,3 +401,69 @@ def test_golden_fig4_total_polarisation():
         m = n[:L] - n[L:]
         assert abs(m.sum() - g["sum_m"]) < 1e-11
         assert abs(m[0]) > 1e-3  # the impurity is polarised at t = 0
+
+
+# ------------------------------------------- Lanczos G(omega), Eq. (gapprox)
+def _dense_resolvent_parts(m, L, orbs, omega, eta):
+    c = jw_parts(L)
+    H = dense_fock_h(m, c)
+    i0 = sector_index(L, m["n_up"], m["n_dn"])
+    w, v = np.linalg.eigh(H[np.ix_(i0, i0)])
+    g = np.zeros(H.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    E0 = w[0]
+    eye = np.eye(H.shape[0])
+    out_g = np.zeros((len(orbs), omega.size), dtype=np.complex128)
+    out_l = np.zeros_like(out_g)
+    for a, (site, spin) in enumerate(orbs):
+        ca = c[spin * L + site]
+        pg, pl = ca.T @ g, ca @ g
+        for k, om in enumerate(omega):
+            out_g[a, k] = pg.conj() @ np.linalg.solve((om + 1j * eta + E0) * eye - H, pg)
+            out_l[a, k] = pl.conj() @ np.linalg.solve((om + 1j * eta - E0) * eye + H, pl)
+    return out_g, out_l, E0, H, g, c
+
+
+def test_green_lanczos_full_krylov_is_exact():
+    """With n at least the sector dimension the Lanczos resolvent is the exact
+    one (Eq. (gomega)): compare with the dense resolvent on the Fock space."""
+    L = 4
+    m = W.random_model(L, 2, 1, seed=41, complex_hopping=True)
+    orbs = [(0, 0), (3, 0), (2, 1)]
+    omega = np.linspace(-5.0, 5.0, 23)
+    Gg, Gl, E0 = oracle.green_lanczos(m, orbs, 40, omega, 0.15)
+    rg, rl, e0, *_ = _dense_resolvent_parts(m, L, orbs, omega, 0.15)
+    assert abs(E0 - e0) < 1e-12
+    assert np.max(np.abs(Gg - rg)) < 1e-11 and np.max(np.abs(Gl - rl)) < 1e-11
+
+
+def test_green_lanczos_moments_and_sum_rule():
+    """With n < d the n-pole function reproduces the first 2n moments
+    <0|c (H - E0)^r c^dag|0> of the high-frequency expansion (Eq. (ghigh) and
+    the remark after it), and the weights of both parts sum to 1."""
+    L = 4
+    m = W.random_model(L, 2, 2, seed=43, complex_hopping=True)
+    site, spin = 1, 0
+    n = 4
+    sec = oracle.Sector(m)
+    E0, psi0, _ = sec.ground_state(K=80, tol=1e-13)
+    *_, H, g, c = _dense_resolvent_parts(m, L, [(site, spin)], np.zeros(1), 0.1)
+    ca = c[spin * L + site]
+    wsum = 0.0
+    for dagger in (True, False):
+        nb = sec.neighbour(spin, dagger)
+        v0 = sec.apply_cop(nb, site, spin, dagger, psi0)
+        a, b, norm0 = oracle.lanczos_run(nb, v0, n)
+        Em, Q = np.linalg.eigh(np.diag(a) + np.diag(b, 1) + np.diag(b, -1))
+        wgt = (norm0 * Q[0, :]) ** 2
+        wsum += wgt.sum()
+        shift = -E0 if dagger else E0  # particle: H - E0; hole: -(H - E0) in the denominator
+        p = (ca.T if dagger else ca) @ g
+        Hs = H - E0 * np.eye(H.shape[0]) if dagger else E0 * np.eye(H.shape[0]) - H
+        x = p.copy()
+        for r in range(2 * n):
+            exact = float((p.conj() @ x).real)
+            lan = float(np.sum(wgt * ((Em + shift) if dagger else (shift - Em)) ** r))
+            assert abs(lan - exact) <= 1e-9 * max(1.0, abs(exact)), (dagger, r, lan, exact)
+            x = Hs @ x
+    assert abs(wsum - 1.0) < 1e-12
