@@ -301,6 +301,7 @@ def run_ours(args):
         batched = batched_vs_plain(args.batch_instances, args.batch_steps)
         adjoint = adjoint_vs_fd()
         spectral = lanczos_spectral(si, opts)
+        spectral["fine_grid"] = fine_grid_vs_plain(si, opts)
 
     if rank == 0:
         clocks = clk.summary()
@@ -405,6 +406,30 @@ def lanczos_spectral(si, opts, n=100):
                         "(d=731808 each), eta=0.1, 2001 frequencies" % n,
             "seconds": round(t, 3), "lanczos_steps_per_s": round(2 * n / t, 1),
             "spectral_weight": round(float(np.trapezoid(A, omega) if hasattr(np, "trapezoid") else np.trapz(A, omega)), 4)}
+
+
+def fine_grid_vs_plain(si, opts, n_steps=400, fine=8):
+    """Equilibrium G_00(t) of the U = 8 ring on 401 times (dt = 0.05): one
+    Krylov space per time step (M = 20) against one per `fine` times with the
+    step exponential at several times (M = 40).  Ground state already
+    computed (untimed); output times per second and the largest difference."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    o40 = kg.kg_opts_default(M=40, reorth=1, stream=opts.stream)
+    kg.kg_green_equilibrium(si.handle, [(0, 0)], 0.05, 4, opts)  # warm-up
+    kg.kg_green_equilibrium_fine(si.handle, [(0, 0)], 0.05, 2 * fine, fine, o40)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gg, Gl = kg.kg_green_equilibrium(si.handle, [(0, 0)], 0.05, n_steps, opts)
+    t1 = time.perf_counter()
+    Fg, Fl = kg.kg_green_equilibrium_fine(si.handle, [(0, 0)], 0.05, n_steps, fine, o40)
+    t2 = time.perf_counter()
+    diff = float(max(np.max(np.abs(Fg - Gg)), np.max(np.abs(Fl - Gl))))
+    return {"workload": "equilibrium G_00(t) of the c2 ring ground state (U=8), 401 times, dt=0.05",
+            "plain_s": round(t1 - t0, 3), "fine_s": round(t2 - t1, 3), "fine": fine, "M_fine": 40,
+            "speedup": round((t1 - t0) / (t2 - t1), 2), "max_abs_diff": diff}
 
 
 def adjoint_vs_fd():

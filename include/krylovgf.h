@@ -197,6 +197,18 @@ int kg_propagate(kg_sector* s, double* x_dev, double dt, int n_steps, const kg_o
 int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps,
                          const kg_opts* o, double* G_gtr, double* G_les);
 
+/* ---- equilibrium Green's function on a fine output grid ---------------
+ * Section 3, Eq. (udelta) evaluated at several times per Krylov space: the
+ * same G as kg_green_equilibrium on t_k = k*dt, k = 0..n_steps, but each
+ * Krylov space (of dimension o->M, built from psi(t)) serves the `fine` times
+ * t + q*dt, q = 1..fine (the last one also starts the next space), so there
+ * are n_steps/fine Krylov builds instead of n_steps.  The Krylov step is
+ * fine*dt: o->M must be large enough for it (the error of one step falls as
+ * (w fine dt / 2)^M / M! with w the spectral width of H).  1 <= fine <= 32;
+ * output as for kg_green_equilibrium. */
+int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, int fine,
+                              const kg_opts* o, double* G_gtr, double* G_les);
+
 /* ---- conventional Lanczos Green's function (frequency domain) ----------
  * Section 2, Eqs. (gomega), (resolv) and (gapprox): for each diagonal orbital
  * alpha = (site, spin), an n-step Lanczos run (full reorthogonalisation) from

@@ -67,6 +67,7 @@ _sig = {
     "kg_green_equilibrium_batched": (_I, [_P, _I, _P, _I, _D, _I, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_green_equilibrium_vjp": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _I, _P, _P, _P, _P, _P, _P]),
     "kg_green_lanczos": (_I, [_P, _P, _I, _I, _P, _I, _D, ctypes.POINTER(Opts), _P, _P, _P]),
+    "kg_green_equilibrium_fine": (_I, [_P, _P, _I, _D, _I, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -206,6 +207,19 @@ def kg_green_equilibrium(handle, orbitals, dt, n_steps, opts=None):
     Gl = np.zeros_like(Gg)
     _check(lib.kg_green_equilibrium(handle, orb.ctypes.data, n, float(dt), int(n_steps), ctypes.byref(o),
                                     Gg.ctypes.data, Gl.ctypes.data), "kg_green_equilibrium")
+    return Gg, Gl
+
+
+def kg_green_equilibrium_fine(handle, orbitals, dt, n_steps, fine, opts=None):
+    """Equilibrium G on the grid t_k = k dt with one Krylov space per `fine`
+    output times (Krylov step fine*dt); same layout as kg_green_equilibrium."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    Gg = np.zeros((n_steps + 1, n, n), dtype=np.complex128)
+    Gl = np.zeros_like(Gg)
+    _check(lib.kg_green_equilibrium_fine(handle, orb.ctypes.data, n, float(dt), int(n_steps), int(fine),
+                                         ctypes.byref(o), Gg.ctypes.data, Gl.ctypes.data), "kg_green_equilibrium_fine")
     return Gg, Gl
 
 
@@ -390,6 +404,9 @@ class Sector:
 
     def green_equilibrium(self, orbitals, dt, n_steps, opts=None):
         return kg_green_equilibrium(self.handle, orbitals, dt, n_steps, opts)
+
+    def green_equilibrium_fine(self, orbitals, dt, n_steps, fine, opts=None):
+        return kg_green_equilibrium_fine(self.handle, orbitals, dt, n_steps, fine, opts)
 
     def green_lanczos(self, orbitals, n, omega, eta, opts=None):
         return kg_green_lanczos(self.handle, orbitals, n, omega, eta, opts)

@@ -217,6 +217,108 @@ static int eq_run(std::vector<EqGroup>& G, const std::vector<kg_sector*>& inst, 
     return rc;
 }
 
+// Fine output grid (Section 3: Eq. (udelta) evaluated at several times from
+// one Krylov space).  Each Krylov space, built from psi(t) with step `fine`
+// dt, serves the times t + q dt, q = 1..fine: psi(t + q dt) = sum_k c^(q)_k V_k
+// with c^(q) = beta0 e^{-iT q dt} e_1 (one multi-time step exponential), so
+// the overlaps with the start vectors are the small products
+// sum_k c^(q)_k <chi_a | V_k> -- the <chi_a | V_k> are one overlap launch per
+// step.  Fills ov exactly as eq_run does.
+static int eq_run_fine(std::vector<EqGroup>& G, const std::vector<kg_sector*>& inst, const int* orb, Krylov& K,
+                       double2* ov, int rows, double dt, int n_steps, int fine, const kg_opts* o, cudaStream_t st) {
+    const int B = K.B, MK = K.M + 1;
+    size_t off = 0;
+    int na_max = 1;
+    for (auto& g : G) {
+        const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+        na_max = std::max(na_max, na);
+        kg_sector* s = inst[g.inst];
+        for (int a = 0; a < na; ++a)
+            KG_TRY(launch_cop(s, g.nb, orb[2 * g.idx[a]], g.spin, g.dagger, s->gs, g.chi + (size_t)a * dn, st));
+        g.ov0 = off;
+        off += (size_t)na * rows * na;
+        KG_TRY(launch_inner_lib(g.chi, na, g.chi, na, dn, ov + g.ov0, rows * na, st));  // row 0
+        for (int a = 0; a < na; ++a)
+            KG_CUDA(cudaMemcpyAsync(K.vec(g.col0 + a, 0), g.chi + (size_t)a * dn, sizeof(double2) * dn,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    if (n_steps == 0) return KG_OK;
+    double2 *P = nullptr, *cq = nullptr;
+    double* taus = nullptr;
+    auto release = [&](int rc) {
+        cudaFree(P);
+        cudaFree(cq);
+        cudaFree(taus);
+        return rc;
+    };
+    if (cudaMalloc(&P, sizeof(double2) * (size_t)B * MK * na_max) != cudaSuccess ||
+        cudaMalloc(&cq, sizeof(double2) * (size_t)B * fine * K.M) != cudaSuccess ||
+        cudaMalloc(&taus, sizeof(double) * (size_t)B * fine) != cudaSuccess) {
+        set_error("fine-grid workspace allocation failed");
+        return release(KG_ENOMEM);
+    }
+    std::vector<double2> hP((size_t)B * MK * na_max), hc((size_t)B * fine * K.M), hov(off);
+    KG_CUDA(cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * off, cudaMemcpyDeviceToHost, st));  // row 0
+    std::vector<ColScalars> hcs(B);
+    std::vector<double> ht((size_t)B * fine);
+    int nq_prev = -1;
+    for (int k0 = 0; k0 < n_steps; k0 += fine) {
+        const int nq = std::min(fine, n_steps - k0);
+        if (nq != nq_prev) {
+            for (auto& g : G)
+                for (size_t a = 0; a < g.idx.size(); ++a)
+                    for (int q = 0; q < nq; ++q)
+                        ht[(size_t)(g.col0 + a) * nq + q] = (g.dagger ? dt : -dt) * (q + 1);
+            if (cudaMemcpyAsync(taus, ht.data(), sizeof(double) * B * nq, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return release(KG_ECUDA);
+            nq_prev = nq;
+        }
+        int rc = build_space(K, o->reorth, st);
+        // <chi_a | V_k> of every column, then c^(q) for every column and time
+        for (auto& g : G) {
+            const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+            for (int a = 0; rc == KG_OK && a < na; ++a)
+                rc = launch_inner_lib(g.chi, na, K.vec(g.col0 + a, 0), MK, dn, P + (size_t)(g.col0 + a) * MK * na_max,
+                                      na_max, st);
+        }
+        if (rc == KG_OK) rc = launch_tridiag_multi(K, taus, nq, cq, st);
+        if (rc != KG_OK) return release(rc);
+        if (cudaMemcpyAsync(hP.data(), P, sizeof(double2) * hP.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hc.data(), cq, sizeof(double2) * (size_t)B * nq * K.M, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(hcs.data(), K.cs, sizeof(ColScalars) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return release(cuda_fail(cudaGetLastError(), "fine-grid readback", __FILE__, __LINE__));
+        for (auto& g : G) {
+            const int na = (int)g.idx.size();
+            for (int bcol = 0; bcol < na; ++bcol) {
+                const int b = g.col0 + bcol, m = hcs[b].m_eff;
+                for (int q = 0; q < nq; ++q)
+                    for (int a = 0; a < na; ++a) {
+                        std::complex<double> acc(0.0, 0.0);
+                        for (int k = 0; k < m; ++k) {
+                            const double2 c = hc[((size_t)b * nq + q) * K.M + k];
+                            const double2 pv = hP[((size_t)b * MK + k) * na_max + a];
+                            acc += std::complex<double>(c.x, c.y) * std::complex<double>(pv.x, pv.y);
+                        }
+                        hov[g.ov0 + ((size_t)bcol * rows + k0 + 1 + q) * na + a] = make_double2(acc.real(), acc.imag());
+                    }
+            }
+        }
+        // psi(t + nq dt) = V c^(nq) becomes the next start vector
+        if (cudaMemcpy2DAsync(reinterpret_cast<char*>(K.cs) + offsetof(ColScalars, c), sizeof(ColScalars),
+                              cq + (size_t)(nq - 1) * K.M, sizeof(double2) * nq * K.M, sizeof(double2) * K.M, B,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return release(KG_ECUDA);
+        rc = launch_combine(K, st);
+        if (rc != KG_OK) return release(rc);
+    }
+    if (cudaMemcpyAsync(ov, hov.data(), sizeof(double2) * off, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return release(KG_ECUDA);
+    return release(KG_OK);
+}
+
 // G entries of one instance from the raw overlaps (host): ov[b][k][a] =
 // <vec_a | propagated vec_b at t_k>; particle gives G^>_{a b}, hole G^<_{b a}.
 static void eq_assemble(const EqGroup& g, const std::vector<double2>& hov, int rows, double dt, double E0, int n_orb,
@@ -243,7 +345,7 @@ static void eq_assemble(const EqGroup& g, const std::vector<double2>& hov, int r
 // column of every instance in one batch.  status[i] receives the ground-state
 // status of instance i (its G stays zero unless KG_OK).
 static int green_eq_batch(kg_sector* const* sv, int n_inst, const int* orb, int n_orb, double dt, int n_steps,
-                          const kg_opts* o, double* G_gtr, double* G_les, int* status, bool tune) {
+                          const kg_opts* o, double* G_gtr, double* G_les, int* status, bool tune, int fine = 0) {
     KG_TRY(check_opts(o));
     if (n_steps < 0 || !G_gtr || !G_les || n_inst < 1) {
         set_error("bad n_steps, n_inst or NULL output");
@@ -289,7 +391,9 @@ static int green_eq_batch(kg_sector* const* sv, int n_inst, const int* orb, int 
     }
     double2* ov = nullptr;
     if (rc == KG_OK && cudaMalloc(&ov, sizeof(double2) * std::max<size_t>(1, n_ov)) != cudaSuccess) rc = KG_ENOMEM;
-    if (rc == KG_OK) rc = eq_run(G, inst, orb, K, ov, rows, dt, n_steps, o, tune, st);
+    if (rc == KG_OK)
+        rc = fine > 0 ? eq_run_fine(G, inst, orb, K, ov, rows, dt, n_steps, fine, o, st)
+                      : eq_run(G, inst, orb, K, ov, rows, dt, n_steps, o, tune, st);
     std::vector<double2> hov(n_ov);
     if (rc == KG_OK &&
         (cudaMemcpyAsync(hov.data(), ov, sizeof(double2) * n_ov, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -739,3 +843,17 @@ int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, dou
 }
 
 }  // namespace kg
+
+extern "C" int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, int fine,
+                                         const kg_opts* o, double* G_gtr, double* G_les) {
+    kg_opts tmp;
+    if (!o) {
+        kg_opts_default(&tmp);
+        o = &tmp;
+    }
+    if (!s || fine < 1 || fine > 32) {
+        kg::set_error("kg_green_equilibrium_fine: need a sector and 1 <= fine <= 32");
+        return KG_EINVAL;
+    }
+    return kg::green_eq_batch(&s, 1, orb, n_orb, dt, n_steps, o, G_gtr, G_les, nullptr, false, fine);
+}

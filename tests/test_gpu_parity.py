@@ -494,3 +494,28 @@ def test_green_lanczos_edges():
     assert np.all(Gg[0] == 0) and np.max(np.abs(Gl - rl)) < G_TOL and np.max(np.abs(Gg - rg)) < G_TOL
     with pytest.raises(kg.KGError):
         s.green_lanczos([(0, 0)], 256, omega, 0.1)
+
+
+# --------------------------- fine output grid, Eq. (udelta) at several times
+def test_fine_grid_one_is_the_plain_path():
+    m = W.random_model(6, 3, 2, seed=21, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (1, 1)]
+    s = kg.Sector(m)
+    Gg, Gl = s.green_equilibrium(orbs, 0.1, 20)
+    Fg, Fl = s.green_equilibrium_fine(orbs, 0.1, 20, 1)
+    assert np.max(np.abs(Fg - Gg)) < 1e-12 and np.max(np.abs(Fl - Gl)) < 1e-12
+
+
+@pytest.mark.parametrize("fine,n", [(4, 40), (5, 37)])
+def test_fine_grid_vs_oracle(fine, n):
+    """Several output times per Krylov space (step fine*dt, M = 40), including
+    a last space that serves fewer times; against the oracle's G(t)."""
+    cfg = W.config_c1()
+    s = kg.Sector(cfg["model"])
+    orbs = [(0, 0), (1, 1)]
+    opts = kg.kg_opts_default(M=40)
+    Gg, Gl = s.green_equilibrium_fine(orbs, 0.05, n, fine, opts)
+    rg, rl, _ = oracle.green_equilibrium(cfg["model"], orbs, 0.05, n)
+    assert np.max(np.abs(Gg - rg)) < G_TOL and np.max(np.abs(Gl - rl)) < G_TOL
+    with pytest.raises(kg.KGError):
+        s.green_equilibrium_fine(orbs, 0.05, n, 33, opts)
