@@ -302,6 +302,7 @@ def run_ours(args):
         adjoint = adjoint_vs_fd()
         spectral = lanczos_spectral(si, opts)
         spectral["fine_grid"] = fine_grid_vs_plain(si, opts)
+        spectral["fourier"] = fourier_transform(fp64)
 
     if rank == 0:
         clocks = clk.summary()
@@ -430,6 +431,36 @@ def fine_grid_vs_plain(si, opts, n_steps=400, fine=8):
     return {"workload": "equilibrium G_00(t) of the c2 ring ground state (U=8), 401 times, dt=0.05",
             "plain_s": round(t1 - t0, 3), "fine_s": round(t2 - t1, 3), "fine": fine, "M_fine": 40,
             "speedup": round((t1 - t0) / (t2 - t1), 2), "max_abs_diff": diff}
+
+
+def fourier_transform(fp64_tflops, n_t=100001, n_omega=4001):
+    """The damped Fourier transform G(t) -> G(omega) at the sampling of the
+    paper's Fig. 1 (dt' = 0.01 up to t_max = 1000, eta = 0.01): a particle
+    and a hole series (synthetic sums of exponentials), 4001 frequencies on
+    [-10, 10], host buffers in and out.  Counted as 8 flops (4 FP64 FMAs)
+    per sample and frequency."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    rng = np.random.default_rng(5)
+    dt = 0.01
+    t = dt * np.arange(n_t)
+    E = rng.uniform(-8.0, 8.0, size=(2, 8))
+    A = rng.uniform(0.0, 1.0, size=(2, 8))
+    G = -1j * np.einsum("sm,smk->sk", A / A.sum(1, keepdims=True), np.exp(-1j * E[:, :, None] * t))
+    omega = np.linspace(-10.0, 10.0, n_omega)
+    kg.kg_green_fourier(G[:, :2048], dt, omega[:512], 0.01)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = kg.kg_green_fourier(G, dt, omega, 0.01)
+    sec = time.perf_counter() - t0
+    tf = 8.0 * G.size * n_omega / sec / 1e12
+    return {"workload": "damped Fourier transform, 2 series x %d samples (dt=0.01, t_max=1000, eta=0.01) onto %d "
+                        "frequencies, host buffers" % (n_t, n_omega),
+            "seconds": round(sec, 4), "tflops_fp64": round(tf, 3), "frac_fp64_measured": round(tf / fp64_tflops, 3),
+            "spectral_weight": round(float(-np.trapezoid(F.imag, omega).sum() / np.pi / 2)
+                                     if hasattr(np, "trapezoid") else float(-np.trapz(F.imag, omega).sum() / np.pi / 2), 4)}
 
 
 def adjoint_vs_fd():

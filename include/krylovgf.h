@@ -229,6 +229,27 @@ int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt
 int kg_green_lanczos(kg_sector* s, const int* orb, int n_orb, int n, const double* omega, int n_omega,
                      double eta, const kg_opts* o, double* G_gtr, double* G_les, double* coef);
 
+/* ---- G(omega) from G(t): the damped Fourier transform ---------------------
+ * Section 3: the frequency-dependent Green's function obtained from the
+ * time-dependent one by Fourier transformation, the Lorentzian broadening eta
+ * entering as the damping e^{-eta t} (time-dependent Lanczos route, Fig. 1).
+ * For each of n_series series sampled at t_k = k dt, k = 0..n_t-1:
+ *   G_w[s][j] = sum_k w_k exp(i (omega_j + i eta) t_k) G_t[s][k],
+ * w_0 = w_{n_t-1} = dt/2 and w_k = dt otherwise (trapezoidal rule on
+ * [0, (n_t-1) dt]; all zero when n_t = 1).  The transform of the particle
+ * part G^>(t) of kg_green_equilibrium is the particle part of Eq. (gomega)
+ * (G_gtr of kg_green_lanczos, exact in the limit dt -> 0, t_max -> inf), the
+ * transform of -G^<(t) the hole part.  Evaluated directly on the caller's
+ * frequencies (no FFT grid), FP64, deterministic.
+ *   G_t: host, complex [n_series][n_t];  omega: host double[n_omega], finite;
+ *   G_w: host, complex [n_series][n_omega] (caller-owned, written);
+ *   0 <= n_series <= 65535, 1 <= n_t <= 2^30, n_omega >= 0, dt > 0, eta >= 0
+ *   (KG_EINVAL otherwise; KG_ENOMEM when the device copies do not fit).
+ * stream as for kg_hpsi; returns after the result is on the host.  Device
+ * memory is stream-ordered scratch (cudaMallocAsync), freed before return. */
+int kg_green_fourier(const double* G_t, int n_series, int n_t, double dt, const double* omega, int n_omega,
+                     double eta, void* stream, double* G_w);
+
 /* ---- batched equilibrium Green's functions ----------------------------
  * The equilibrium Green's functions of n_inst independent sectors (for
  * example the repeated impurity solves of DMFT/VCA-type embedding schemes,

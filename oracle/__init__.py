@@ -17,7 +17,9 @@ exactly as the paper defines them:
       |0> = ground state of H_ini, Phi(t) = e^{-iHt}|0>,
       Psi_a(t) = e^{iHt} c_a Phi(t),  chi_a(t) = e^{iHt} c^dag_a Phi(t),
       G^<_{aa'}(t,t') = i <Psi_a'(t') | Psi_a(t)>,
-      G^>_{aa'}(t,t') = -i <chi_a(t) | chi_a'(t')>.
+      G^>_{aa'}(t,t') = -i <chi_a(t) | chi_a'(t')>;
+* G(omega) from G(t): the damped Fourier transform of Section 3 (trapezoidal
+  rule on the sampled times).
 
 Every propagation here is a Chebyshev expansion over the whole interval
 (never the GPU's restarted Krylov steps), so the two sides are independent.
@@ -269,6 +271,30 @@ def green_lanczos(model, orbitals, n, omega, eta, gs=None, K=80, tol=1e-12):
                 else:
                     G[i] += wgt[m] / (omega + 1j * eta + Em[m] - E0)
     return G_gtr, G_les, E0
+
+
+def green_fourier(G_t, dt, omega, eta):
+    """G(omega) from a sampled G(t) (Section 3: Fourier transformation of the
+    time-dependent Green's function, made convergent at t_max by the damping
+    e^{-eta t} of the broadening).  The time integral over [0, (n_t-1) dt] is
+    the trapezoidal rule on t_k = k dt:
+        G(omega) = sum_k w_k e^{i (omega + i eta) t_k} G(t_k),
+        w_0 = w_{n_t-1} = dt/2, w_k = dt otherwise (no interval: zero).
+    G_t: complex [n_series, n_t] or [n_t]; returns [n_series, n_omega] or
+    [n_omega]."""
+    g = np.asarray(G_t, dtype=np.complex128)
+    one = g.ndim == 1
+    g = g.reshape(1, -1) if one else g
+    omega = np.asarray(omega, dtype=np.float64).ravel()
+    n_t = g.shape[1]
+    out = np.zeros((g.shape[0], omega.size), dtype=np.complex128)
+    if n_t >= 2:
+        t = dt * np.arange(n_t)
+        w = np.full(n_t, float(dt))
+        w[0] = w[-1] = 0.5 * dt
+        kernel = np.exp(1j * np.outer(omega + 1j * eta, t))  # [n_omega, n_t]
+        out = (g * w) @ kernel.T
+    return out[0] if one else out
 
 
 def keldysh_vectors(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):

@@ -68,6 +68,7 @@ _sig = {
     "kg_green_equilibrium_vjp": (_I, [_P, _P, _I, _D, _I, ctypes.POINTER(Opts), _I, _P, _P, _P, _P, _P, _P]),
     "kg_green_lanczos": (_I, [_P, _P, _I, _I, _P, _I, _D, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_green_equilibrium_fine": (_I, [_P, _P, _I, _D, _I, _I, ctypes.POINTER(Opts), _P, _P]),
+    "kg_green_fourier": (_I, [_P, _I, _I, _D, _P, _I, _D, _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -276,6 +277,22 @@ def kg_green_lanczos(handle, orbitals, n, omega, eta, opts=None):
     return Gg, Gl, coef
 
 
+def kg_green_fourier(G_t, dt, omega, eta, stream=None):
+    """Damped Fourier transform sum_k w_k e^{i(omega + i eta) t_k} G(t_k),
+    t_k = k dt, trapezoidal weights, of each row of G_t (complex [n_series,
+    n_t], or one series [n_t]); returns complex [n_series, n_omega] (or
+    [n_omega] for one series)."""
+    g = np.ascontiguousarray(np.asarray(G_t, dtype=np.complex128))
+    one = g.ndim == 1
+    g = g.reshape(1, -1) if one else g.reshape(g.shape[0], g.shape[-1])
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).ravel())
+    out = np.zeros((g.shape[0], w.size), dtype=np.complex128)
+    _check(lib.kg_green_fourier(g.ctypes.data if g.size else None, g.shape[0], g.shape[1], float(dt),
+                                w.ctypes.data if w.size else None, w.size, float(eta), _stream(stream),
+                                out.ctypes.data if out.size else None), "kg_green_fourier")
+    return out[0] if one else out
+
+
 def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):
     o = opts if opts is not None else kg_opts_default()
     orb = _orb_array(orbitals)
@@ -410,6 +427,20 @@ class Sector:
 
     def green_lanczos(self, orbitals, n, omega, eta, opts=None):
         return kg_green_lanczos(self.handle, orbitals, n, omega, eta, opts)
+
+    def spectrum_td(self, orbitals, dt, n_steps, omega, eta, fine=1, opts=None):
+        """Time-dependent Lanczos G(omega) of the diagonal orbitals: the
+        equilibrium G(t_k), k = 0..n_steps (one Krylov space per `fine`
+        times), then its damped Fourier transform.  Returns (G_gtr, G_les),
+        complex [n_orb, n_omega], in the convention of green_lanczos."""
+        if fine == 1:
+            Gg, Gl = kg_green_equilibrium(self.handle, orbitals, dt, n_steps, opts)
+        else:
+            Gg, Gl = kg_green_equilibrium_fine(self.handle, orbitals, dt, n_steps, fine, opts)
+        n = Gg.shape[1]
+        series = np.concatenate([Gg[:, range(n), range(n)].T, -Gl[:, range(n), range(n)].T])
+        out = kg_green_fourier(series, dt, omega, eta, None if opts is None else opts.stream)
+        return out[:n], out[n:]
 
 
 class Keldysh:

@@ -78,5 +78,29 @@ def test_argument_validation_before_device_use(kg):
     assert lib.kg_ground_state(None, None, None, None, None) == kg.KG_EINVAL
     assert lib.kg_keldysh_row(None, 0, None, None) == kg.KG_EINVAL
     assert lib.kg_green_lanczos(None, None, 0, 0, None, 0, 0.0, None, None, None, None) == kg.KG_EINVAL
+
+
+def test_fourier_validation_and_empty_cases(kg):
+    """kg_green_fourier rejects bad sizes and non-finite scalars before any
+    device call; the empty and single-sample cases need no device either."""
+    lib = kg.lib
+    g = np.ones(8, dtype=np.complex128)
+    w = np.linspace(-1.0, 1.0, 3)
+    out = np.zeros(3, dtype=np.complex128)
+    for n_series, n_t, dt, eta in [(-1, 4, 0.1, 0.0), (1, 0, 0.1, 0.0), (1, 4, 0.0, 0.0), (1, 4, -0.1, 0.0),
+                                   (1, 4, float("nan"), 0.0), (1, 4, 0.1, -1.0), (1, 4, 0.1, float("inf")),
+                                   (70000, 4, 0.1, 0.0)]:
+        rc = lib.kg_green_fourier(g.ctypes.data, n_series, n_t, dt, w.ctypes.data, 3, eta, None, out.ctypes.data)
+        assert rc == kg.KG_EINVAL, (n_series, n_t, dt, eta)
+    assert lib.kg_green_fourier(None, 1, 4, 0.1, w.ctypes.data, 3, 0.0, None, out.ctypes.data) == kg.KG_EINVAL
+    bad = np.array([0.0, float("nan"), 1.0])
+    assert lib.kg_green_fourier(g.ctypes.data, 1, 4, 0.1, bad.ctypes.data, 3, 0.0, None,
+                                out.ctypes.data) == kg.KG_EINVAL
+    assert "omega[1]" in kg.kg_last_error()
+    # nothing to transform, and a single sample (an empty time interval)
+    assert kg.kg_green_fourier(np.zeros((2, 5)), 0.1, [], 0.2).shape == (2, 0)
+    assert kg.kg_green_fourier(np.zeros((0, 5)), 0.1, w, 0.2).shape == (0, 3)
+    z = kg.kg_green_fourier(np.array([[1.0 + 2.0j], [3.0j]]), 0.1, w, 0.2)
+    assert z.shape == (2, 3) and np.all(z == 0)
     lib.kg_free_sector(None)
     lib.kg_keldysh_free(None)

@@ -467,3 +467,66 @@ def test_green_lanczos_moments_and_sum_rule():
             assert abs(lan - exact) <= 1e-9 * max(1.0, abs(exact)), (dagger, r, lan, exact)
             x = Hs @ x
     assert abs(wsum - 1.0) < 1e-12
+
+
+# ---------------------------------- G(omega) from G(t), the damped transform
+def _trapezoid_exp(lam, dt, n_t):
+    """sum_k w_k e^{i lam t_k}, t_k = k dt, trapezoidal weights, summed in
+    closed form as a geometric series in z = e^{i lam dt}."""
+    if n_t < 2:
+        return np.zeros_like(lam, dtype=np.complex128)
+    z = np.exp(1j * lam * dt)
+    return dt * ((1 - z ** n_t) / (1 - z) - 0.5 * (1 + z ** (n_t - 1)))
+
+
+def test_fourier_geometric_series():
+    """A sum of exponentials transforms into the closed-form geometric sums:
+    pins the weights (end points halved), the sign of omega and of eta, and
+    the time index of every sample."""
+    rng = np.random.default_rng(61)
+    E = np.array([-2.3, 0.4, 5.1])
+    A = rng.normal(size=(2, 3)) + 1j * rng.normal(size=(2, 3))
+    omega = np.linspace(-6.05, 6.05, 37)  # no omega equals a pole E
+    for dt, n_t, eta in ((0.05, 1000, 0.0), (0.1, 7, 0.3), (0.2, 2, 0.1), (0.1, 1, 0.2)):
+        t = dt * np.arange(n_t)
+        G = A @ np.exp(-1j * np.outer(E, t))  # two series
+        F = oracle.green_fourier(G, dt, omega, eta)
+        ref = sum(A[:, m, None] * _trapezoid_exp(omega - E[m] + 1j * eta, dt, n_t)[None, :] for m in range(3))
+        assert F.shape == (2, omega.size)
+        assert np.max(np.abs(F - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref))), (dt, n_t, eta)
+        assert np.max(np.abs(oracle.green_fourier(G[1], dt, omega, eta) - F[1])) <= 1e-12 * max(1.0, np.max(np.abs(F)))
+
+
+def test_fourier_of_equilibrium_G_is_the_lehmann_sum():
+    """The transform of the oracle's G^>(t) and of -G^<(t) equals the same
+    trapezoidal sums taken over the Lehmann poles and weights of a dense eigh
+    of the Fock-space H, and approaches the resolvent of Eq. (gomega) (the
+    particle and hole parts) as dt -> 0 with e^{-eta t_max} negligible."""
+    L = 4
+    m = W.random_model(L, 2, 1, seed=47, complex_hopping=True)
+    orbs = [(1, 0), (2, 1)]
+    dt, n, eta = 0.01, 6000, 0.5  # t_max = 60, e^{-30}
+    omega = np.linspace(-5.0, 5.0, 41)
+    Gg, Gl, E0 = oracle.green_equilibrium(m, orbs, dt, n)
+    rg, rl, e0, H, g, c = _dense_resolvent_parts(m, L, orbs, omega, eta)
+    assert abs(E0 - e0) < 1e-12
+    Ew, Vw = np.linalg.eigh(H)
+    for a, (site, spin) in enumerate(orbs):
+        ca = c[spin * L + site]
+        Fg = oracle.green_fourier(Gg[:, a, a], dt, omega, eta)
+        Fl = oracle.green_fourier(-Gl[:, a, a], dt, omega, eta)
+        wg = np.abs(Vw.conj().T @ (ca.T @ g)) ** 2  # |<m|c^dag_a 0>|^2
+        wl = np.abs(Vw.conj().T @ (ca @ g)) ** 2    # |<m|c_a 0>|^2
+        lg = -1j * sum(wg[k] * _trapezoid_exp(omega - (Ew[k] - E0) + 1j * eta, dt, n + 1)
+                       for k in range(Ew.size) if wg[k] > 1e-15)
+        ll = -1j * sum(wl[k] * _trapezoid_exp(omega + (Ew[k] - E0) + 1j * eta, dt, n + 1)
+                       for k in range(Ew.size) if wl[k] > 1e-15)
+        assert np.max(np.abs(Fg - lg)) < 1e-9 and np.max(np.abs(Fl - ll)) < 1e-9
+        # the quadrature error of the trapezoidal rule is (|lambda| dt)^2 / 12
+        # relative, |lambda| <= 12 here
+        scale = max(np.max(np.abs(rg[a])), np.max(np.abs(rl[a])))
+        assert np.max(np.abs(Fg - rg[a])) < 2e-3 * scale
+        assert np.max(np.abs(Fl - rl[a])) < 2e-3 * scale
+        # causality: -Im of both parts is positive (the trapezoidal sum of a
+        # damped exponential has a positive real part)
+        assert np.min(-Fg.imag) > 0 and np.min(-Fl.imag) > 0
