@@ -587,12 +587,18 @@ def main():
     ap.add_argument("--ref-gsteps", type=int, default=4)
     ap.add_argument("--ncu-case", action="store_true", help="small case for full ncu captures")
     ap.add_argument("--ncu-orbitals", type=int, default=6, help="orbitals of the ncu case (12 = the full row)")
+    ap.add_argument("--fourier-case", action="store_true",
+                    help="only the damped Fourier transform extra (for ncu captures of k_fourier)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint comparisons")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=100)
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)
+        return
+    if args.fourier_case:
+        import paper_1109_1205_gb300 as kg
+        print(json.dumps({"fourier_case": fourier_transform(kg.kg_probe_fp64(None))}))
         return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
