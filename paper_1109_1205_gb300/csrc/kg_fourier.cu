@@ -146,10 +146,35 @@ static int green_fourier(const double* G_t, int n_series, int n_t, double dt, co
     const int n_wtiles = (n_omega + kFtThreads - 1) / kFtThreads;
     const int n_tiles = (int)((n_t + kFtTile - 1) / kFtTile);
     const long long base = (long long)n_wtiles * n_series;
-    const int want = (int)std::max(1LL, (4LL * nsm + base - 1) / base);
-    int n_split = std::min(want, n_tiles);
-    const int tiles_per_split = (n_tiles + n_split - 1) / n_split;
-    n_split = (n_tiles + tiles_per_split - 1) / tiles_per_split;  // no empty split
+    // Split count: the resident blocks of an SM share its FP64 pipe, so an
+    // SM's time is the number of tiles its blocks hold, and the launch ends
+    // with the busiest SM, ceil(blocks / nsm) blocks of tiles_per_split tiles
+    // (plus a small per-block cost).  Take the split count that minimises
+    // this, the fewest splits among equals, over at most a few waves, with at
+    // least 4 blocks (16 warps) per SM where the series is long enough: the
+    // Horner chains need that many warps to keep the FP64 pipe busy.
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fourier, kFtThreads, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long max_split = std::max(1LL, std::min<long long>(n_tiles, 4LL * per_sm * nsm / base + 1));
+    const long long min_split = std::min(max_split, (4LL * nsm + base - 1) / base);
+    int n_split = 1, tiles_per_split = n_tiles;
+    double best = -1.0;
+    for (int pass = 0; pass < 2 && best < 0.0; ++pass)
+        for (long long ns = pass == 0 ? min_split : 1; ns <= max_split; ++ns) {
+            const int tps = (int)((n_tiles + ns - 1) / ns);
+            if ((n_tiles + tps - 1) / tps != ns) continue;  // would leave a split empty
+            const long long busiest = (base * ns + nsm - 1) / nsm;
+            const double cost = (double)busiest * (tps + 0.05);
+            if (best < 0.0 || cost < best) {
+                best = cost;
+                n_split = (int)ns;
+                tiles_per_split = tps;
+            }
+        }
 
     // device copies: the series, the frequencies, the partial planes, the result
     const size_t b_gt = sizeof(double2) * (size_t)n_series * n_t;
