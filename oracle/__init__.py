@@ -19,7 +19,10 @@ exactly as the paper defines them:
       G^<_{aa'}(t,t') = i <Psi_a'(t') | Psi_a(t)>,
       G^>_{aa'}(t,t') = -i <chi_a(t) | chi_a'(t')>;
 * G(omega) from G(t): the damped Fourier transform of Section 3 (trapezoidal
-  rule on the sampled times).
+  rule on the sampled times);
+* the Matsubara and mixed components named after step (iv) of Section 4, at
+  zero temperature with a chemical potential mu on the imaginary branch
+  (imaginary-time propagators from dense eigen-decompositions, small sectors).
 
 Every propagation here is a Chebyshev expansion over the whole interval
 (never the GPU's restarted Krylov steps), so the two sides are independent.
@@ -347,6 +350,103 @@ def green_keldysh(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):
                         for ib, b in enumerate(idx):
                             G_gtr[k, l, a, b] = -1j * np.vdot(Chi[spin][k][ia], Chi[spin][l][ib])
     return G_les, G_gtr, E0
+
+
+def dense_hamiltonian(sector):
+    """The sector Hamiltonian as a dense matrix, one column H e_j per basis
+    state (small sectors only)."""
+    d = sector.dim
+    if d > 4096:
+        raise ValueError("dense_hamiltonian is for sectors of dimension <= 4096")
+    H = np.empty((d, d), dtype=np.complex128)
+    e = np.zeros(d, dtype=np.complex128)
+    for j in range(d):
+        e[j] = 1.0
+        H[:, j] = sector.hpsi(e)
+        e[j] = 0.0
+    return H
+
+
+def _imaginary_time_vectors(sector, x, taus, shift):
+    """e^{-(H - shift) tau} x for every tau of taus, from the eigen-
+    decomposition of the dense sector H: rows of the returned array."""
+    w, Q = np.linalg.eigh(dense_hamiltonian(sector))
+    px = Q.conj().T @ x
+    return np.stack([Q @ (np.exp(-(w - shift) * tau) * px) for tau in taus])
+
+
+def green_matsubara(model, orbitals, taus, mu, gs=None, K=80, tol=1e-12):
+    """The Matsubara function of the initial-state Hamiltonian at zero
+    temperature (Section 4, after step (iv): G^M(tau, tau') = G^M(tau - tau'),
+    the equilibrium Green's function of H_ini on the imaginary branch), with
+    the chemical potential mu in K = H - mu N:
+        G^M_{aa'}(+tau) = -<0| c_a e^{-(H - E0 - mu) tau} c^dag_a' |0>,
+        G^M_{aa'}(-tau) = +<0| c^dag_a' e^{-(H - E0 + mu) tau} c_a |0>,
+    for tau >= 0 (the two one-sided limits at tau = 0).  The imaginary-time
+    propagators come from the eigen-decomposition of the dense neighbour-
+    sector H (small sectors).  Returns (G_plus, G_minus, E0), each
+    [n_tau, n_orb, n_orb] with G_plus[j] = G^M(tau_j), G_minus[j] =
+    G^M(-tau_j)."""
+    sec = Sector(model)
+    E0, psi0, _ = sec.ground_state(K=K, tol=tol) if gs is None else gs
+    taus = np.asarray(taus, dtype=np.float64).ravel()
+    n = len(orbitals)
+    G_plus = np.zeros((taus.size, n, n), dtype=np.complex128)
+    G_minus = np.zeros_like(G_plus)
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger in (True, False):
+            nb = sec.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            vecs = {a: sec.apply_cop(nb, orbitals[a][0], spin, dagger, psi0) for a in idx}
+            shift = E0 + mu if dagger else E0 - mu
+            for p in idx:
+                prop = _imaginary_time_vectors(nb, vecs[p], taus, shift)  # [n_tau, d]
+                for a in idx:
+                    ov = prop @ vecs[a].conj()  # <vecs[a] | prop(tau)>
+                    if dagger:
+                        G_plus[:, a, p] = -ov
+                    else:
+                        G_minus[:, p, a] = ov
+    return G_plus, G_minus, E0
+
+
+def green_mixed(ini, fin, orbitals, dt, n_t, taus, mu, gs=None, K=80, tol=1e-12):
+    """The mixed real/imaginary-time components of Section 4 (after step
+    (iv)) at zero temperature, initial state |0> of H_ini, K = H_ini - mu N on
+    the imaginary branch:
+        G^right_{aa'}(t_k, tau_j) = +i <xi_a'(tau_j) | Psi_a(t_k)>,
+        G^left_{aa'}(tau_j, t_k)  = -i <zeta_a(tau_j) | chi_a'(t_k)>,
+    with Psi_a(t) = e^{iHt} c_a Phi(t), chi_a(t) = e^{iHt} c^dag_a Phi(t) of
+    steps (ii)-(iii) (H = H_fin) and the imaginary-time vectors
+        xi_a(tau) = e^{-(H_ini - E0 + mu) tau} c_a |0>,
+        zeta_a(tau) = e^{-(H_ini - E0 - mu) tau} c^dag_a |0>.
+    Returns (G_right [n_t, n_tau, n, n], G_left [n_tau, n_t, n, n], E0)."""
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    _, _, Psi, Chi = keldysh_vectors(ini, fin, orbitals, dt, n_t, gs=(E0, psi0, 0.0))
+    taus = np.asarray(taus, dtype=np.float64).ravel()
+    n = len(orbitals)
+    G_right = np.zeros((n_t, taus.size, n, n), dtype=np.complex128)
+    G_left = np.zeros((taus.size, n_t, n, n), dtype=np.complex128)
+    for spin, idx in _groups(orbitals).items():
+        for dagger, store in ((False, Psi), (True, Chi)):
+            if spin not in store:
+                continue
+            nb = sec_i.neighbour(spin, dagger)
+            shift = E0 + mu if dagger else E0 - mu
+            imag = {a: _imaginary_time_vectors(nb, sec_i.apply_cop(nb, orbitals[a][0], spin, dagger, psi0), taus,
+                                               shift) for a in idx}
+            for k in range(n_t):
+                for ia, a in enumerate(idx):
+                    for ib, b in enumerate(idx):
+                        if not dagger:  # G^right_{ab}(t_k, tau) = i <xi_b(tau) | Psi_a(t_k)>
+                            G_right[k, :, a, b] = 1j * (imag[b].conj() @ store[spin][k][ia])
+                        else:  # G^left_{ab}(tau, t_k) = -i <zeta_a(tau) | chi_b(t_k)>
+                            G_left[:, k, a, b] = -1j * (imag[a].conj() @ store[spin][k][ib])
+    return G_right, G_left, E0
 
 
 def keldysh_entry(ini, fin, orbital_a, orbital_b, dt, k, l, gs=None, K=80, tol=1e-12):

@@ -530,3 +530,137 @@ def test_fourier_of_equilibrium_G_is_the_lehmann_sum():
         # causality: -Im of both parts is positive (the trapezoidal sum of a
         # damped exponential has a positive real part)
         assert np.min(-Fg.imag) > 0 and np.min(-Fl.imag) > 0
+
+
+# ------------------------ Matsubara and mixed components (zero temperature)
+def _n_total(c):
+    return sum(ck.T @ ck for ck in c)
+
+
+def test_matsubara_vs_jordan_wigner():
+    """G^M(+tau) = -<0|c_a e^{-tau (K - K0)} c^dag_b|0> and G^M(-tau) =
+    <0|c^dag_b e^{-tau (K - K0)} c_a|0> with K = H - mu N, computed with scipy
+    expm on the full Fock space built from Jordan-Wigner matrices."""
+    L = 4
+    m = W.random_model(L, 2, 1, seed=51, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (1, 1), (3, 1)]
+    taus = np.array([0.0, 0.3, 1.1, 2.5])
+    mu = 0.2
+    Gp, Gm, E0 = oracle.green_matsubara(m, orbs, taus, mu)
+    c = jw_parts(L)
+    H = dense_fock_h(m, c)
+    i0 = sector_index(L, 2, 1)
+    w, v = np.linalg.eigh(H[np.ix_(i0, i0)])
+    assert abs(E0 - w[0]) < 1e-12
+    g = np.zeros(H.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    Kd = H - mu * _n_total(c) - (E0 - 3 * mu) * np.eye(H.shape[0])  # K - K0
+    for j, tau in enumerate(taus):
+        P = sla.expm(-tau * Kd)
+        for a, (ia, sa) in enumerate(orbs):
+            for b, (ib, sb) in enumerate(orbs):
+                ca, cb = c[sa * L + ia], c[sb * L + ib]
+                assert abs(Gp[j, a, b] - (-(g.conj() @ ca @ P @ cb.T @ g))) < 1e-12
+                assert abs(Gm[j, a, b] - (g.conj() @ cb.T @ P @ ca @ g)) < 1e-12
+    # the jump at tau = 0: G^M(0+) - G^M(0-) = -<{c_a, c^dag_b}> = -delta_ab
+    assert np.max(np.abs(Gp[0] - Gm[0] + np.eye(4))) < 1e-12
+
+
+def test_matsubara_and_mixed_U0_closed_form():
+    """Free fermions (complex hopping, a quench of hopping and on-site
+    energies): G^M(+tau) = -[e^{-(h-mu)tau}(1-rho)], G^M(-tau) =
+    [e^{(h-mu)tau} rho], G^right(t,tau) = i[e^{-i h_f t} rho e^{(h_i-mu)tau}],
+    G^left(tau,t) = -i[e^{-(h_i-mu)tau}(1-rho) e^{i h_f t}], rho[k,l] =
+    <c^dag_l c_k> of the initial ground state."""
+    L = 6
+    ini = W.random_model(L, 3, 2, seed=53, complex_hopping=True)
+    fin = W.random_model(L, 3, 2, seed=54, complex_hopping=True)
+    ini["U"][:] = 0.0
+    fin["U"][:] = 0.0
+    orbs = [(0, 0), (3, 0), (5, 0), (1, 1), (4, 1)]
+    taus = np.array([0.0, 0.4, 1.7])
+    mu, dt, nt = 0.1, 0.25, 4
+    Gp, Gm, _ = oracle.green_matsubara(ini, orbs, taus, mu)
+    Gr, Gf, _ = oracle.green_mixed(ini, fin, orbs, dt, nt, taus, mu)
+    for spin, N in ((0, 3), (1, 2)):
+        hi = ini["h"] + np.diag(ini["eps"][spin])
+        hf = fin["h"] + np.diag(fin["eps"][spin])
+        w, v = np.linalg.eigh(hi)
+        assert w[N] - w[N - 1] > 1e-3  # closed shell
+        rho = v[:, :N] @ v[:, :N].conj().T
+        one = np.eye(L)
+        idx = [k for k, o in enumerate(orbs) if o[1] == spin]
+        for j, tau in enumerate(taus):
+            Em = sla.expm(-(hi - mu * one) * tau)
+            Ep = sla.expm((hi - mu * one) * tau)
+            ref_p, ref_m = -Em @ (one - rho), Ep @ rho
+            for k in range(nt):
+                Uf = sla.expm(-1j * hf * dt * k)
+                ref_r = 1j * Uf @ rho @ Ep
+                ref_f = -1j * Em @ (one - rho) @ Uf.conj().T
+                for a in idx:
+                    for b in idx:
+                        i, jj = orbs[a][0], orbs[b][0]
+                        assert abs(Gr[k, j, a, b] - ref_r[i, jj]) < 1e-12
+                        assert abs(Gf[j, k, a, b] - ref_f[i, jj]) < 1e-12
+            for a in idx:
+                for b in idx:
+                    i, jj = orbs[a][0], orbs[b][0]
+                    assert abs(Gp[j, a, b] - ref_p[i, jj]) < 1e-12
+                    assert abs(Gm[j, a, b] - ref_m[i, jj]) < 1e-12
+    # opposite spins never mix
+    assert np.all(Gr[:, :, :3, 3:] == 0) and np.all(Gf[:, :, 3:, :3] == 0)
+
+
+def test_mixed_interacting_quench_vs_jordan_wigner():
+    """Interacting quench on L = 3: G^right_{ab}(t,tau) = i<0|c^dag_b(tau)
+    c_a(t)|0> and G^left_{ab}(tau,t) = -i<0|c_a(tau) c^dag_b(t)|0> with
+    imaginary-time operators of K_ini = H_ini - mu N and real-time ones of
+    H_fin, from expm on the Jordan-Wigner Fock space; and the boundary
+    relations G^left(tau, 0) = i G^M(tau), G^right(0, tau) = i G^M(-tau)."""
+    L = 3
+    ini = W.random_model(L, 2, 1, seed=57, complex_hopping=True)
+    fin = W.random_model(L, 2, 1, seed=57, complex_hopping=True)
+    fin["U"] = 0.5 * ini["U"] + 1.0
+    fin["eps"] = ini["eps"] - 0.3
+    orbs = [(0, 0), (2, 0), (1, 1)]
+    taus = np.array([0.0, 0.5, 1.3])
+    mu, dt, nt = -0.15, 0.3, 5
+    Gr, Gf, E0 = oracle.green_mixed(ini, fin, orbs, dt, nt, taus, mu)
+    Gp, Gm, _ = oracle.green_matsubara(ini, orbs, taus, mu)
+    c = jw_parts(L)
+    Hi, Hf = dense_fock_h(ini, c), dense_fock_h(fin, c)
+    i0 = sector_index(L, 2, 1)
+    w, v = np.linalg.eigh(Hi[np.ix_(i0, i0)])
+    assert abs(E0 - w[0]) < 1e-12
+    g = np.zeros(Hi.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    Kd = Hi - mu * _n_total(c) - (E0 - 3 * mu) * np.eye(Hi.shape[0])
+    for j, tau in enumerate(taus):
+        P = sla.expm(-tau * Kd)
+        for k in range(nt):
+            U = sla.expm(-1j * Hf * dt * k)
+            for a, (ia, sa) in enumerate(orbs):
+                for b, (ib, sb) in enumerate(orbs):
+                    ca, cb = c[sa * L + ia], c[sb * L + ib]
+                    ref_r = 1j * (g.conj() @ cb.T @ P @ U.conj().T @ ca @ U @ g)
+                    ref_f = -1j * (g.conj() @ ca @ P @ U.conj().T @ cb.T @ U @ g)
+                    assert abs(Gr[k, j, a, b] - ref_r) < 1e-11
+                    assert abs(Gf[j, k, a, b] - ref_f) < 1e-11
+    assert np.max(np.abs(Gf[:, 0] - 1j * Gp)) < 1e-12
+    assert np.max(np.abs(Gr[0] - 1j * Gm)) < 1e-12
+
+
+def test_matsubara_hubbard_atom():
+    """Half-filled atom, eps = -U/2, mu = 0: adding or removing an electron
+    costs U/2, so the spin-averaged G^M(+tau) = -e^{-U tau/2}/2 and
+    G^M(-tau) = e^{-U tau/2}/2."""
+    U = 2.6
+    taus = np.linspace(0.0, 3.0, 7)
+    Gp = Gm = 0
+    for nu, nd in ((1, 0), (0, 1)):
+        m = W.make_model(1, nu, nd, np.zeros((1, 1)), np.full((2, 1), -U / 2), np.array([U]))
+        p, q, _ = oracle.green_matsubara(m, [(0, 0), (0, 1)], taus, 0.0)
+        Gp, Gm = Gp + 0.25 * (p[:, 0, 0] + p[:, 1, 1]), Gm + 0.25 * (q[:, 0, 0] + q[:, 1, 1])
+    assert np.max(np.abs(Gp + 0.5 * np.exp(-U * taus / 2))) < 1e-14
+    assert np.max(np.abs(Gm - 0.5 * np.exp(-U * taus / 2))) < 1e-14
