@@ -58,6 +58,7 @@ _sig = {
     "kg_neighbour_dim": (_I, [_P, _I, _I, ctypes.POINTER(_LL)]),
     "kg_apply_cop": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "kg_overlaps": (_I, [_P, _I, _P, _I, _LL, _P, _P]),
+    "kg_overlaps_noalloc": (_I, [_P, _I, _P, _I, _LL, _P, _P]),
     "kg_ground_state": (_I, [_P, ctypes.POINTER(Opts), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)]),
     "kg_copy_ground_state": (_I, [_P, _P, _I]),
@@ -180,6 +181,12 @@ def kg_overlaps(X_dev, n_x, Y_dev, n_y, d, G_dev, stream=None):
     """G[b][a] = <x_a|y_b> on the device (complex [n_y][n_x])."""
     _check(lib.kg_overlaps(_addr(X_dev), int(n_x), _addr(Y_dev), int(n_y), int(d), _addr(G_dev), _stream(stream)),
            "kg_overlaps")
+
+
+def kg_overlaps_noalloc(X_dev, n_x, Y_dev, n_y, d, G_dev, stream=None):
+    """kg_overlaps without device allocation (library-held scratch, n_y <= 64)."""
+    _check(lib.kg_overlaps_noalloc(_addr(X_dev), int(n_x), _addr(Y_dev), int(n_y), int(d), _addr(G_dev),
+                                   _stream(stream)), "kg_overlaps_noalloc")
 
 
 def kg_ground_state(handle, opts=None):

@@ -43,6 +43,15 @@ def test_every_declared_symbol_is_exported(kg):
     assert set(declared_functions()) <= exported
 
 
+def test_binding_declares_every_signature(kg):
+    """The ctypes binding gives every declared function its argument types,
+    so no pointer or 64-bit size goes through ctypes' default int conversion."""
+    from paper_1109_1205_gb300 import _lib
+    for name in declared_functions():
+        assert name in _lib._sig, name
+        assert getattr(kg.lib, name).argtypes is not None, name
+
+
 def test_options_and_status_strings(kg):
     o = kg.kg_opts_default()
     assert (o.M, o.M_gs, o.reorth, o.use_graphs, o.seed) == (20, 100, 1, 1, 1234)
@@ -104,3 +113,43 @@ def test_fourier_validation_and_empty_cases(kg):
     assert z.shape == (2, 3) and np.all(z == 0)
     lib.kg_free_sector(None)
     lib.kg_keldysh_free(None)
+
+
+def test_every_handle_entry_rejects_null(kg):
+    """Each entry point that takes a handle or buffers returns KG_EINVAL for
+    NULL before any device call (and the free functions accept NULL)."""
+    lib = kg.lib
+    o = kg.kg_opts_default()
+    ob = ctypes.byref(o)
+    buf = np.zeros(64)
+    b = buf.ctypes.data
+    orb = np.zeros(2, dtype=np.int32)
+    ll = ctypes.c_longlong()
+    E = kg.KG_EINVAL
+    assert lib.kg_sector_dims(None, None, None, None) == E
+    assert lib.kg_sector_strings(None, None, None) == E
+    assert lib.kg_neighbour_dim(None, 0, 1, ctypes.byref(ll)) == E
+    assert lib.kg_apply_cop(None, 0, 0, 1, b, b, None) == E
+    assert lib.kg_copy_ground_state(None, b, 1) == E
+    assert lib.kg_propagate(None, b, 0.1, 1, ob) == E
+    assert lib.kg_green_equilibrium(None, orb.ctypes.data, 1, 0.1, 1, ob, b, b) == E
+    assert lib.kg_green_equilibrium_fine(None, orb.ctypes.data, 1, 0.1, 1, 2, ob, b, b) == E
+    assert lib.kg_green_equilibrium_batched(None, 0, orb.ctypes.data, 1, 0.1, 1, ob, b, b, None) == E
+    nulls = (ctypes.c_void_p * 2)()
+    assert lib.kg_green_equilibrium_batched(nulls, 2, orb.ctypes.data, 1, 0.1, 1, ob, b, b, None) == E
+    assert "NULL sector" in kg.kg_last_error()
+    assert lib.kg_green_equilibrium_vjp(None, orb.ctypes.data, 1, 0.1, 1, ob, 0, None, None, b, b, b, b) == E
+    assert lib.kg_green_keldysh(None, None, orb.ctypes.data, 1, 0.1, 1, ob, b, b) == E
+    assert lib.kg_keldysh_create(None, None, orb.ctypes.data, 1, 0.1, 1, ob, None) == E
+    assert lib.kg_keldysh_gram(None, b, b) == E
+    assert lib.kg_keldysh_get_phi(None, 0, b) == E
+    assert lib.kg_keldysh_set_phi(None, 0, b) == E
+    assert lib.kg_overlaps(None, 1, b, 1, 4, b, None) == E
+    assert lib.kg_overlaps(b, 0, b, 1, 4, b, None) == E
+    assert lib.kg_overlaps(b, 33, b, 1, 4, b, None) == E
+    assert lib.kg_overlaps_noalloc(b, 1, None, 1, 4, b, None) == E
+    assert lib.kg_overlaps_noalloc(b, 1, b, 65, 4, b, None) == E
+    assert lib.kg_probe_fp64(None, None) == E
+    lib.kg_free_sector(None)
+    lib.kg_keldysh_free(None)
+    lib.kg_opts_default(None)
