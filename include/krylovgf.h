@@ -229,6 +229,26 @@ int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt
 int kg_green_lanczos(kg_sector* s, const int* orb, int n_orb, int n, const double* omega, int n_omega,
                      double eta, const kg_opts* o, double* G_gtr, double* G_les, double* coef);
 
+/* ---- zero-temperature Matsubara function (conventional Lanczos route) ----
+ * Section 4, after step (iv): the Matsubara Green's function is the
+ * equilibrium Green's function of the (initial-state) Hamiltonian on the
+ * imaginary branch.  With K = H - mu N and the ground state |0> of s:
+ *   G_plus[a][j]  = G^M_aa(+tau_j) = -<0| c_a e^{-(H - E0 - mu) tau_j} c^dag_a |0>,
+ *   G_minus[a][j] = G^M_aa(-tau_j) = +<0| c^dag_a e^{-(H - E0 + mu) tau_j} c_a |0>,
+ * evaluated from the n-step Lanczos runs of kg_green_lanczos (the same GPU
+ * batch) through the Ritz pairs of each tridiagonal matrix (Eq. (eigen)),
+ * found on the host by cyclic Jacobi rotations.  Exact when the Krylov space
+ * exhausts the sector; otherwise the error falls faster than exponentially
+ * in n at fixed tau.  mu should lie between the removal and addition
+ * energies (E0 - E0(N-1) <= mu <= E0(N+1) - E0) for decaying functions.
+ *   orb: host int[2 n_orb] (site, spin) pairs; 1 <= n <= 255; mu finite;
+ *   tau: host double[n_tau], each finite and >= 0;
+ *   G_plus, G_minus: host double[n_orb][n_tau] (real: diagonal orbitals).
+ * Runs kg_ground_state first if needed.  A part whose neighbour sector does
+ * not exist is zero. */
+int kg_green_matsubara(kg_sector* s, const int* orb, int n_orb, int n, double mu, const double* tau, int n_tau,
+                       const kg_opts* o, double* G_plus, double* G_minus);
+
 /* ---- G(omega) from G(t): the damped Fourier transform ---------------------
  * Section 3: the frequency-dependent Green's function obtained from the
  * time-dependent one by Fourier transformation, the Lorentzian broadening eta

@@ -70,6 +70,7 @@ _sig = {
     "kg_green_lanczos": (_I, [_P, _P, _I, _I, _P, _I, _D, ctypes.POINTER(Opts), _P, _P, _P]),
     "kg_green_equilibrium_fine": (_I, [_P, _P, _I, _D, _I, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_fourier": (_I, [_P, _I, _I, _D, _P, _I, _D, _P, _P]),
+    "kg_green_matsubara": (_I, [_P, _P, _I, _I, _D, _P, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -284,6 +285,22 @@ def kg_green_lanczos(handle, orbitals, n, omega, eta, opts=None):
     return Gg, Gl, coef
 
 
+def kg_green_matsubara(handle, orbitals, n, mu, tau, opts=None):
+    """Zero-temperature Matsubara function of the diagonal orbitals from
+    n-step Lanczos runs: returns (G_plus, G_minus), real [n_orb, n_tau], with
+    G_plus[a, j] = G^M_aa(+tau_j) and G_minus[a, j] = G^M_aa(-tau_j)."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n_orb = orb.shape[0]
+    t = np.ascontiguousarray(np.asarray(tau, dtype=np.float64).ravel())
+    Gp = np.zeros((n_orb, t.size), dtype=np.float64)
+    Gm = np.zeros_like(Gp)
+    _check(lib.kg_green_matsubara(handle, orb.ctypes.data, n_orb, int(n), float(mu), t.ctypes.data if t.size else None,
+                                  t.size, ctypes.byref(o), Gp.ctypes.data if Gp.size else None,
+                                  Gm.ctypes.data if Gm.size else None), "kg_green_matsubara")
+    return Gp, Gm
+
+
 def kg_green_fourier(G_t, dt, omega, eta, stream=None):
     """Damped Fourier transform sum_k w_k e^{i(omega + i eta) t_k} G(t_k),
     t_k = k dt, trapezoidal weights, of each row of G_t (complex [n_series,
@@ -434,6 +451,9 @@ class Sector:
 
     def green_lanczos(self, orbitals, n, omega, eta, opts=None):
         return kg_green_lanczos(self.handle, orbitals, n, omega, eta, opts)
+
+    def green_matsubara(self, orbitals, n, mu, tau, opts=None):
+        return kg_green_matsubara(self.handle, orbitals, n, mu, tau, opts)
 
     def spectrum_td(self, orbitals, dt, n_steps, omega, eta, fine=1, opts=None):
         """Time-dependent Lanczos G(omega) of the diagonal orbitals: the

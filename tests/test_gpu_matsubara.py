@@ -1,0 +1,71 @@
+"""GPU parity of the zero-temperature Matsubara function (Section 4, after
+step (iv)) from the conventional Lanczos runs against the oracle's dense
+imaginary-time propagators.  Tolerance 1e-11 relative to max(1, |G|) where
+the Krylov space exhausts the sector, 1e-10 where it does not (the
+imaginary-time exponential of a 150-step Krylov space of the 300-dimensional
+star-SIAM sectors is exact to rounding for tau <= 10)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1109_1205_gb300 as kg  # noqa: E402
+
+
+def diag(G):
+    return np.stack([G[:, a, a] for a in range(G.shape[1])])
+
+
+def test_matsubara_exhausted_krylov_space():
+    m = W.random_model(5, 2, 2, seed=61, complex_hopping=True)
+    orbs = [(0, 0), (3, 0), (2, 1)]
+    taus = np.array([0.0, 0.2, 1.0, 3.0, 7.0])
+    mu = 0.15
+    s = kg.Sector(m)
+    Gp, Gm = s.green_matsubara(orbs, 120, mu, taus)
+    Rp, Rm, _ = oracle.green_matsubara(m, orbs, taus, mu)
+    Rp, Rm = diag(Rp), diag(Rm)
+    assert np.max(np.abs(Rp.imag)) < 1e-13 and np.max(np.abs(Rm.imag)) < 1e-13
+    scale = np.maximum(1.0, np.maximum(np.abs(Rp.real), np.abs(Rm.real)))
+    assert np.max(np.abs(Gp - Rp.real) / scale) < 1e-11 and np.max(np.abs(Gm - Rm.real) / scale) < 1e-11
+    # the jump at tau = 0: G^M(0+) - G^M(0-) = -1
+    assert np.max(np.abs(Gp[:, 0] - Gm[:, 0] + 1.0)) < 1e-12
+    s.close()
+
+
+def test_matsubara_star_siam():
+    cfg = W.config_c1()
+    orbs = [(0, 0), (2, 1)]
+    taus = np.linspace(0.0, 10.0, 21)
+    s = kg.Sector(cfg["model"])
+    Gp, Gm = s.green_matsubara(orbs, 150, 0.0, taus)
+    Rp, Rm, _ = oracle.green_matsubara(cfg["model"], orbs, taus, 0.0)
+    assert np.max(np.abs(Gp - diag(Rp).real)) < 1e-10 and np.max(np.abs(Gm - diag(Rm).real)) < 1e-10
+    # particle-hole symmetric impurity: G^M_00(-tau) = -G^M_00(+tau); decaying with tau
+    assert np.max(np.abs(Gm[0] + Gp[0])) < 1e-10
+    assert np.all(np.diff(-Gp[0]) < 0)
+    s.close()
+
+
+def test_matsubara_edges():
+    # full up band: no particle part for spin up
+    m = W.make_model(3, 3, 1, W.chain_hopping(3), None, [2.0, 1.0, 0.5])
+    s = kg.Sector(m)
+    taus = np.array([0.0, 0.5])
+    Gp, Gm = s.green_matsubara([(0, 0), (1, 1)], 10, 0.3, taus)
+    Rp, Rm, _ = oracle.green_matsubara(m, [(0, 0), (1, 1)], taus, 0.3)
+    assert np.all(Gp[0] == 0)
+    assert np.max(np.abs(Gp - diag(Rp).real)) < 1e-11 and np.max(np.abs(Gm - diag(Rm).real)) < 1e-11
+    assert s.green_matsubara([(0, 0)], 10, 0.0, []) [0].shape == (1, 0)
+    for bad in (dict(n=256, tau=taus), dict(n=10, tau=[-0.1]), dict(n=10, tau=[float("nan")])):
+        with pytest.raises(kg.KGError):
+            s.green_matsubara([(0, 0)], bad["n"], 0.0, bad["tau"])
+    with pytest.raises(kg.KGError):
+        s.green_matsubara([(0, 0)], 10, float("inf"), taus)
+    s.close()
