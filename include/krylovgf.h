@@ -249,6 +249,20 @@ int kg_green_lanczos(kg_sector* s, const int* orb, int n_orb, int n, const doubl
 int kg_green_matsubara(kg_sector* s, const int* orb, int n_orb, int n, double mu, const double* tau, int n_tau,
                        const kg_opts* o, double* G_plus, double* G_minus);
 
+/* ---- zero-temperature Matsubara function on a tau grid ------------------
+ * The same G^M as kg_green_matsubara, for every orbital pair of one spin, on
+ * tau_k = k dtau, k = 0..n_steps, by imaginary-time Krylov steps: each vector
+ * c^dag_b|0> (c_b|0>) is carried from tau to tau + dtau by Eq. (udelta) with
+ * the exponential e^{-(T - s) dtau} of the step's Lanczos matrix, s = E0 + mu
+ * (E0 - mu); o->M sets the Krylov dimension of a step.
+ *   G_plus[k][a][b]  = G^M_ab(+tau_k) = -<0| c_a e^{-(H - E0 - mu) tau_k} c^dag_b |0>,
+ *   G_minus[k][a][b] = G^M_ab(-tau_k) = +<0| c^dag_b e^{-(H - E0 + mu) tau_k} c_a |0>,
+ * host, complex [(n_steps+1)][n_orb][n_orb]; entries of opposite spins are
+ * zero.  n_steps >= 0, dtau > 0 and mu finite (KG_EINVAL otherwise).  Runs
+ * kg_ground_state first if needed. */
+int kg_green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau, int n_steps,
+                             const kg_opts* o, double* G_plus, double* G_minus);
+
 /* ---- G(omega) from G(t): the damped Fourier transform ---------------------
  * Section 3: the frequency-dependent Green's function obtained from the
  * time-dependent one by Fourier transformation, the Lorentzian broadening eta

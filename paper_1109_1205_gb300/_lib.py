@@ -71,6 +71,7 @@ _sig = {
     "kg_green_equilibrium_fine": (_I, [_P, _P, _I, _D, _I, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_fourier": (_I, [_P, _I, _I, _D, _P, _I, _D, _P, _P]),
     "kg_green_matsubara": (_I, [_P, _P, _I, _I, _D, _P, _I, ctypes.POINTER(Opts), _P, _P]),
+    "kg_green_matsubara_steps": (_I, [_P, _P, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
@@ -301,6 +302,20 @@ def kg_green_matsubara(handle, orbitals, n, mu, tau, opts=None):
     return Gp, Gm
 
 
+def kg_green_matsubara_steps(handle, orbitals, mu, dtau, n_steps, opts=None):
+    """Zero-temperature Matsubara function on tau_k = k dtau by imaginary-time
+    Krylov steps: returns (G_plus, G_minus), complex [n_steps+1, n_orb, n_orb]
+    with G_plus[k, a, b] = G^M_ab(+tau_k) and G_minus[k, a, b] = G^M_ab(-tau_k)."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    Gp = np.zeros((n_steps + 1, n, n), dtype=np.complex128)
+    Gm = np.zeros_like(Gp)
+    _check(lib.kg_green_matsubara_steps(handle, orb.ctypes.data, n, float(mu), float(dtau), int(n_steps),
+                                        ctypes.byref(o), Gp.ctypes.data, Gm.ctypes.data), "kg_green_matsubara_steps")
+    return Gp, Gm
+
+
 def kg_green_fourier(G_t, dt, omega, eta, stream=None):
     """Damped Fourier transform sum_k w_k e^{i(omega + i eta) t_k} G(t_k),
     t_k = k dt, trapezoidal weights, of each row of G_t (complex [n_series,
@@ -454,6 +469,9 @@ class Sector:
 
     def green_matsubara(self, orbitals, n, mu, tau, opts=None):
         return kg_green_matsubara(self.handle, orbitals, n, mu, tau, opts)
+
+    def green_matsubara_steps(self, orbitals, mu, dtau, n_steps, opts=None):
+        return kg_green_matsubara_steps(self.handle, orbitals, mu, dtau, n_steps, opts)
 
     def spectrum_td(self, orbitals, dt, n_steps, omega, eta, fine=1, opts=None):
         """Time-dependent Lanczos G(omega) of the diagonal orbitals: the

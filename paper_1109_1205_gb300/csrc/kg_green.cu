@@ -551,6 +551,192 @@ int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<doub
     return rc;
 }
 
+// ------------------------------------------ Matsubara function on a tau grid
+// Section 4, after step (iv): the zero-temperature Matsubara function of H for
+// every orbital pair of one spin on tau_k = k dtau, by imaginary-time Krylov
+// steps.  Each column's vector (c^dag_b|0> for the particle part, c_b|0> for
+// the hole part) goes from tau to tau + dtau by the step of Eq. (udelta) with
+// the imaginary-time exponential, psi' = ||psi|| V e^{-(T - s) dtau} e_1,
+// s = E0 + mu (particle) or E0 - mu (hole).  The Krylov spaces, the overlaps
+// <vec_a | V_k> and the combination run on the GPU (the kernels of the fine
+// output grid); the m-dimensional exponential is a Taylor series on the host
+// (substeps with ||T - s||_inf h <= 1/2, 18 terms).
+
+// Coefficients on the stored (unnormalised) basis: out[k] = beta0 scale_k
+// [e^{-(T - s) dtau} e_1]_k for k < m_eff, zero up to M.
+static void imag_step_coefficients(const ColScalars& c, double shift, double dtau, int M, double2* out) {
+    const int m = c.m_eff;
+    for (int k = 0; k < M; ++k) out[k] = make_double2(0.0, 0.0);
+    if (m == 0) return;
+    std::vector<double> v(m, 0.0), term(m), y(m), sum(m);
+    v[0] = 1.0;
+    double g = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const double bl = k >= 1 ? c.beta[k] : 0.0, br = k + 1 < m ? c.beta[k + 1] : 0.0;
+        g = std::max(g, std::fabs(c.alpha[k] - shift) + std::fabs(bl) + std::fabs(br));
+    }
+    const int nsub = std::max(1, (int)std::ceil(2.0 * g * dtau));
+    const double h = dtau / nsub;
+    for (int sub = 0; sub < nsub; ++sub) {
+        term = v;
+        sum = v;
+        for (int n = 1; n <= 18; ++n) {
+            for (int k = 0; k < m; ++k) {
+                double t = (c.alpha[k] - shift) * term[k];
+                if (k >= 1) t += c.beta[k] * term[k - 1];
+                if (k + 1 < m) t += c.beta[k + 1] * term[k + 1];
+                y[k] = t;
+            }
+            for (int k = 0; k < m; ++k) {
+                term[k] = -(h / n) * y[k];
+                sum[k] += term[k];
+            }
+        }
+        v = sum;
+    }
+    for (int k = 0; k < m; ++k) out[k] = make_double2(c.beta0 * c.scale[k] * v[k], 0.0);
+}
+
+int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau, int n_steps,
+                          const kg_opts* o, double* G_plus, double* G_minus) {
+    KG_TRY(check_opts(o));
+    if (n_steps < 0 || !(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(mu) || !G_plus || !G_minus) {
+        set_error("kg_green_matsubara_steps: need n_steps >= 0, finite dtau > 0, finite mu and output buffers");
+        return KG_EINVAL;
+    }
+    KG_TRY(check_orbitals(s, orb, n_orb));
+    const int rows = n_steps + 1;
+    const size_t per = (size_t)rows * n_orb * n_orb * 2;
+    std::memset(G_plus, 0, sizeof(double) * per);
+    std::memset(G_minus, 0, sizeof(double) * per);
+    KG_TRY(ensure_gs(s, o));
+    std::vector<EqGroup> G;
+    std::vector<const kg_sector*> cols;
+    eq_groups(G, cols, s, 0, orb, n_orb);
+    if (cols.empty()) return KG_OK;
+    cudaStream_t st = pick_stream(s, o);
+    Krylov K;
+    double2 *ov0 = nullptr, *P = nullptr, *cq = nullptr;
+    auto release = [&](int rc) {
+        for (auto& g : G) cudaFree(g.chi);
+        cudaFree(ov0);
+        cudaFree(P);
+        cudaFree(cq);
+        krylov_free(K);
+        return rc;
+    };
+    const int rc_alloc = krylov_alloc(K, cols, o->M, s->nsm, o->schedule);
+    if (rc_alloc != KG_OK) return release(rc_alloc);
+    const int B = K.B, MK = K.M + 1;
+    size_t off = 0;
+    int na_max = 1;
+    for (auto& g : G) {
+        const size_t na = g.idx.size();
+        na_max = std::max(na_max, (int)na);
+        g.ov0 = off;
+        off += na * rows * na;
+        if (cudaMalloc(&g.chi, sizeof(double2) * na * g.nb->d) != cudaSuccess) {
+            set_error("Matsubara workspace allocation failed");
+            return release(KG_ENOMEM);
+        }
+    }
+    if (cudaMalloc(&ov0, sizeof(double2) * (size_t)na_max * na_max * G.size()) != cudaSuccess ||
+        cudaMalloc(&P, sizeof(double2) * (size_t)B * MK * na_max) != cudaSuccess ||
+        cudaMalloc(&cq, sizeof(double2) * (size_t)B * K.M) != cudaSuccess) {
+        set_error("Matsubara workspace allocation failed");
+        return release(KG_ENOMEM);
+    }
+    // start vectors and row 0 (tau = 0): <vec_a | vec_b>
+    std::vector<double2> hov(off), h0((size_t)na_max * na_max * G.size());
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+        const EqGroup& g = G[gi];
+        const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+        for (int a = 0; a < na; ++a) {
+            int rc = launch_cop(s, g.nb, orb[2 * g.idx[a]], g.spin, g.dagger, s->gs, g.chi + (size_t)a * dn, st);
+            if (rc != KG_OK) return release(rc);
+            if (cudaMemcpyAsync(K.vec(g.col0 + a, 0), g.chi + (size_t)a * dn, sizeof(double2) * dn,
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return release(cuda_fail(cudaGetLastError(), "Matsubara start vectors", __FILE__, __LINE__));
+        }
+        const int rc = launch_inner_lib(g.chi, na, g.chi, na, dn, ov0 + gi * na_max * na_max, na, st);
+        if (rc != KG_OK) return release(rc);
+    }
+    if (cudaMemcpyAsync(h0.data(), ov0, sizeof(double2) * h0.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return release(cuda_fail(cudaGetLastError(), "Matsubara row 0", __FILE__, __LINE__));
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+        const EqGroup& g = G[gi];
+        const int na = (int)g.idx.size();
+        for (int bcol = 0; bcol < na; ++bcol)
+            for (int a = 0; a < na; ++a)
+                hov[g.ov0 + (size_t)bcol * rows * na + a] = h0[gi * na_max * na_max + (size_t)bcol * na + a];
+    }
+    std::vector<double2> hP((size_t)B * MK * na_max), hc((size_t)B * K.M);
+    std::vector<ColScalars> hcs(B);
+    for (int k = 1; k <= n_steps; ++k) {
+        int rc = build_space(K, o->reorth, st);
+        for (auto& g : G) {
+            const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+            for (int a = 0; rc == KG_OK && a < na; ++a)
+                rc = launch_inner_lib(g.chi, na, K.vec(g.col0 + a, 0), MK, dn, P + (size_t)(g.col0 + a) * MK * na_max,
+                                      na_max, st);
+        }
+        if (rc != KG_OK) return release(rc);
+        if (cudaMemcpyAsync(hP.data(), P, sizeof(double2) * hP.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hcs.data(), K.cs, sizeof(ColScalars) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return release(cuda_fail(cudaGetLastError(), "Matsubara readback", __FILE__, __LINE__));
+        for (auto& g : G) {
+            const int na = (int)g.idx.size();
+            const double shift = g.dagger ? s->E0 + mu : s->E0 - mu;
+            for (int bcol = 0; bcol < na; ++bcol) {
+                const int b = g.col0 + bcol, m = hcs[b].m_eff;
+                if (hcs[b].status == KG_ENUMERIC) {
+                    set_error("non-finite value during the imaginary-time steps");
+                    return release(KG_ENUMERIC);
+                }
+                double2* c = hc.data() + (size_t)b * K.M;
+                imag_step_coefficients(hcs[b], shift, dtau, K.M, c);
+                for (int a = 0; a < na; ++a) {
+                    std::complex<double> acc(0.0, 0.0);
+                    for (int kk = 0; kk < m; ++kk) {
+                        const double2 pv = hP[((size_t)b * MK + kk) * na_max + a];
+                        acc += c[kk].x * std::complex<double>(pv.x, pv.y);
+                    }
+                    hov[g.ov0 + ((size_t)bcol * rows + k) * na + a] = make_double2(acc.real(), acc.imag());
+                }
+            }
+        }
+        // psi(tau + dtau) = V c becomes the next start vector
+        if (cudaMemcpyAsync(cq, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpy2DAsync(reinterpret_cast<char*>(K.cs) + offsetof(ColScalars, c), sizeof(ColScalars), cq,
+                              sizeof(double2) * K.M, sizeof(double2) * K.M, B, cudaMemcpyDeviceToDevice,
+                              st) != cudaSuccess)
+            return release(cuda_fail(cudaGetLastError(), "Matsubara coefficients", __FILE__, __LINE__));
+        rc = launch_combine(K, st);
+        if (rc != KG_OK) return release(rc);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return release(cuda_fail(cudaGetLastError(), "Matsubara steps", __FILE__, __LINE__));
+    // G_plus[k][a][b] = -<c^dag_a 0 | psi_b>; G_minus[k][b][a] = <c_a 0 | psi_b>
+    for (auto& g : G) {
+        const int na = (int)g.idx.size();
+        for (int k = 0; k < rows; ++k)
+            for (int bcol = 0; bcol < na; ++bcol)
+                for (int a = 0; a < na; ++a) {
+                    const double2 v = hov[g.ov0 + ((size_t)bcol * rows + k) * na + a];
+                    const int r = g.dagger ? g.idx[a] : g.idx[bcol];
+                    const int c = g.dagger ? g.idx[bcol] : g.idx[a];
+                    const double sg = g.dagger ? -1.0 : 1.0;
+                    double* out =
+                        (g.dagger ? G_plus : G_minus) + ((size_t)k * n_orb * n_orb + (size_t)r * n_orb + c) * 2;
+                    out[0] = sg * v.x;
+                    out[1] = sg * v.y;
+                }
+    }
+    return release(KG_OK);
+}
+
 }  // namespace kg
 
 // ------------------------------------------------------------- Keldysh
@@ -843,6 +1029,20 @@ int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, dou
 }
 
 }  // namespace kg
+
+extern "C" int kg_green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau,
+                                        int n_steps, const kg_opts* o, double* G_plus, double* G_minus) {
+    if (!s) {
+        kg::set_error("NULL sector");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    if (!o) {
+        kg_opts_default(&tmp);
+        o = &tmp;
+    }
+    return kg::green_matsubara_steps(s, orb, n_orb, mu, dtau, n_steps, o, G_plus, G_minus);
+}
 
 extern "C" int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, int fine,
                                          const kg_opts* o, double* G_gtr, double* G_les) {

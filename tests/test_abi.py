@@ -150,6 +150,7 @@ def test_every_handle_entry_rejects_null(kg):
     assert lib.kg_overlaps_noalloc(b, 1, None, 1, 4, b, None) == E
     assert lib.kg_overlaps_noalloc(b, 1, b, 65, 4, b, None) == E
     assert lib.kg_green_matsubara(None, orb.ctypes.data, 1, 10, 0.0, b, 1, ob, b, b) == E
+    assert lib.kg_green_matsubara_steps(None, orb.ctypes.data, 1, 0.0, 0.1, 1, ob, b, b) == E
     assert lib.kg_probe_fp64(None, None) == E
     lib.kg_free_sector(None)
     lib.kg_keldysh_free(None)

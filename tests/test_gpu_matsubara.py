@@ -69,3 +69,30 @@ def test_matsubara_edges():
     with pytest.raises(kg.KGError):
         s.green_matsubara([(0, 0)], 10, float("inf"), taus)
     s.close()
+
+
+@pytest.mark.parametrize("case", ["random", "star"])
+def test_matsubara_steps_full_matrix(case):
+    """Every orbital pair of each spin on tau_k = k dtau by imaginary-time
+    Krylov steps (M = 20 per step), against the oracle's dense propagators;
+    the diagonal also against the Lanczos route."""
+    if case == "random":
+        m = W.random_model(5, 2, 2, seed=61, complex_hopping=True)
+        orbs, mu, dtau, n = [(0, 0), (3, 0), (1, 1), (4, 1)], 0.15, 0.1, 30
+    else:
+        m = W.config_c1()["model"]
+        orbs, mu, dtau, n = [(0, 0), (1, 0), (2, 1)], 0.0, 0.25, 40
+    s = kg.Sector(m)
+    Gp, Gm = s.green_matsubara_steps(orbs, mu, dtau, n)
+    taus = dtau * np.arange(n + 1)
+    Rp, Rm, _ = oracle.green_matsubara(m, orbs, taus, mu)
+    scale = max(1.0, np.max(np.abs(Rp)), np.max(np.abs(Rm)))
+    assert np.max(np.abs(Gp - Rp)) < 1e-10 * scale and np.max(np.abs(Gm - Rm)) < 1e-10 * scale
+    # tau = 0: G^M(0+) - G^M(0-) = -delta within each spin
+    same = np.array([[o1[1] == o2[1] for o2 in orbs] for o1 in orbs])
+    assert np.max(np.abs((Gp[0] - Gm[0])[same] + np.eye(len(orbs))[same])) < 1e-12
+    Lp, Lm = s.green_matsubara(orbs, 120, mu, taus)
+    assert np.max(np.abs(diag(Gp).real - Lp)) < 1e-10 * scale and np.max(np.abs(diag(Gm).real - Lm)) < 1e-10 * scale
+    with pytest.raises(kg.KGError):
+        s.green_matsubara_steps(orbs, mu, -0.1, 2)
+    s.close()
