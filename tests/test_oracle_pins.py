@@ -664,3 +664,19 @@ def test_matsubara_hubbard_atom():
         Gp, Gm = Gp + 0.25 * (p[:, 0, 0] + p[:, 1, 1]), Gm + 0.25 * (q[:, 0, 0] + q[:, 1, 1])
     assert np.max(np.abs(Gp + 0.5 * np.exp(-U * taus / 2))) < 1e-14
     assert np.max(np.abs(Gm - 0.5 * np.exp(-U * taus / 2))) < 1e-14
+
+
+def test_keldysh_entry_matches_the_gram_route():
+    """The single-entry route used for sampled full-size parity equals the
+    full Gram-matrix route (itself pinned to Jordan-Wigner expm and the
+    free-fermion closed forms) for off-diagonal times, both spins and a
+    complex-hopping quench -- a swapped time or orbital index fails."""
+    ini = W.random_model(4, 2, 1, seed=71, complex_hopping=True)
+    fin = W.random_model(4, 2, 1, seed=72, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (1, 1), (3, 1)]
+    dt, nt = 0.2, 5
+    Gl, Gg, _ = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    for (k, l) in ((0, 3), (4, 1), (2, 2)):
+        for a, b in ((0, 1), (1, 0), (2, 3), (0, 2)):
+            les, gtr = oracle.keldysh_entry(ini, fin, orbs[a], orbs[b], dt, k, l)
+            assert abs(les - Gl[k, l, a, b]) < 1e-12 and abs(gtr - Gg[k, l, a, b]) < 1e-12, (k, l, a, b)
