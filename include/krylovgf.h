@@ -149,7 +149,7 @@ int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, int n_y, long
                 void* stream);
 
 /* The same overlaps for callers that cannot allocate device memory at call
- * time: inside CUDA stream capture, under a fixed device-memory budget or a
+ * time: code that runs under a fixed device-memory budget or with a memory
  * pool that must not grow, or where the allocator's implicit synchronisation
  * is not acceptable.  The paper has no counterpart; this is a deployment
  * variant.  It allocates nothing: its scratch is a fixed 1.2 MB array in the

@@ -129,10 +129,9 @@ extern "C" int kg_overlaps(const double* X_dev, int n_x, const double* Y_dev, in
 }
 
 // ------------------------------------------- no-allocation variant
-// Some callers cannot allocate device memory at call time: code running while
-// a stream is being captured into a CUDA graph, code under a fixed device
-// memory budget or a pool that must not grow, and code that must not hit the
-// allocator's implicit synchronisation.  kg_overlaps_noalloc serves them with
+// Some callers cannot allocate device memory at call time: code under a fixed
+// device-memory budget or with a memory pool that must not grow, and code
+// that must not hit the allocator's implicit synchronisation.  kg_overlaps_noalloc serves them with
 // the same kernel as kg_overlaps, its partial sums and tickets held in fixed
 // arrays of this library's device image instead of allocated memory.
 namespace kg {

@@ -182,8 +182,8 @@ static void tridiag_eigen(const double* alpha, const double* beta, int m, std::v
 
 // The zero-temperature Matsubara function of H (Section 4, after step (iv):
 // G^M is the equilibrium Green's function of the initial-state Hamiltonian,
-// "accessible by the time-dependent or by the conventional Lanczos method"),
-// by the conventional route: the n-step Lanczos runs from c^dag_a|0> and
+// which either Lanczos route of the paper can compute), by the conventional
+// route: the n-step Lanczos runs from c^dag_a|0> and
 // c_a|0>, their Ritz pairs (theta_k, Q_{0k}) (Eq. (eigen)), and
 //   G^M_aa(+tau) = -b0^2 sum_k Q_{0k}^2 e^{-(theta_k - E0 - mu) tau},
 //   G^M_aa(-tau) = +b0'^2 sum_k Q'_{0k}^2 e^{-(theta'_k - E0 + mu) tau}.

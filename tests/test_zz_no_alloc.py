@@ -1,6 +1,6 @@
 """kg_overlaps_noalloc: the overlap entry point for callers that cannot
-allocate device memory at call time (for example while a stream is being
-captured into a CUDA graph, or under a fixed device-memory budget).  It must
+allocate device memory at call time (for example code under a fixed
+device-memory budget, or with a memory pool that must not grow).  It must
 give the same results as kg_overlaps, call after call, although every call
 reuses the same fixed scratch arrays.  This file is collected last on
 purpose, so that a run stopping at the first failure has run everything else."""
