@@ -70,6 +70,7 @@ def _load():
     lib.ko_num_threads.restype = I
     lib.ko_set_num_threads.argtypes = [I]
     lib.ko_hpsi.argtypes = [P, P, P]
+    lib.ko_dense_h.argtypes = [P, P]
     lib.ko_apply_cop.restype = I
     lib.ko_apply_cop.argtypes = [P, P, I, I, I, P, P]
     lib.ko_ground_state.restype = I
@@ -353,17 +354,13 @@ def green_keldysh(ini, fin, orbitals, dt, n_t, gs=None, K=80, tol=1e-12):
 
 
 def dense_hamiltonian(sector):
-    """The sector Hamiltonian as a dense matrix, one column H e_j per basis
-    state (small sectors only)."""
+    """The sector Hamiltonian as a dense matrix (small sectors only): every
+    term of H*psi written to its own entry, H[s, k] = <s|H|k>."""
     d = sector.dim
-    if d > 4096:
-        raise ValueError("dense_hamiltonian is for sectors of dimension <= 4096")
+    if d > 5000:
+        raise ValueError("dense_hamiltonian is for sectors of dimension <= 5000")
     H = np.empty((d, d), dtype=np.complex128)
-    e = np.zeros(d, dtype=np.complex128)
-    for j in range(d):
-        e[j] = 1.0
-        H[:, j] = sector.hpsi(e)
-        e[j] = 0.0
+    _load().ko_dense_h(sector.h, _ptr(H))
     return H
 
 
@@ -474,3 +471,213 @@ def keldysh_entry(ini, fin, orbital_a, orbital_b, dt, k, l, gs=None, K=80, tol=1
         vb = nb.propagate(sec_f.apply_cop(nb, sb, pb, dagger, phi_l), -tl)
         out.append(1j * np.vdot(vb, va) if not dagger else -1j * np.vdot(va, vb))
     return out[0], out[1]
+
+
+def _eigh(H):
+    """eigh of a Hermitian matrix, in real arithmetic when H is real."""
+    if not np.any(H.imag):
+        return np.linalg.eigh(H.real)
+    return np.linalg.eigh(H)
+
+
+def _sandwich(Q, Z):
+    """conj(Q) Z Q^T (real products when Q is real)."""
+    if np.isrealobj(Q):
+        return (Q @ Z.real @ Q.T) + 1j * (Q @ Z.imag @ Q.T)
+    return Q.conj() @ Z @ Q.T
+
+
+def _divided_differences(g, dg, E, tol=1e-6):
+    """D[m, n] = (g(E_m) - g(E_n)) / (E_m - E_n), the first divided
+    difference of a function known on the eigenvalues E (values g, derivatives
+    dg); pairs closer than tol take the mean derivative instead."""
+    diff = E[:, None] - E[None, :]
+    close = np.abs(diff) <= tol
+    D = (g[:, None] - g[None, :]) / np.where(close, 1.0, diff)
+    return np.where(close, 0.5 * (dg[:, None] + dg[None, :]), D)
+
+
+def _unit_model(model, kind, i, j=None):
+    """The model whose Hamiltonian is dH/dtheta for one parameter theta (H is
+    linear in h, eps and U): kind 'eps' (theta = eps[i, j] with i the spin),
+    'U' (U_i), 're' / 'im' (the real / imaginary part of h_ij with h_ji tied
+    to its conjugate; i == j is the diagonal h_ii)."""
+    L = model["L"]
+    h = np.zeros((L, L), dtype=np.complex128)
+    eps = np.zeros((2, L))
+    U = np.zeros(L)
+    if kind == "eps":
+        eps[i, j] = 1.0
+    elif kind == "U":
+        U[i] = 1.0
+    elif kind == "re":
+        h[i, j] += 1.0
+        if i != j:
+            h[j, i] += 1.0
+    else:
+        h[i, j] += 1j
+        h[j, i] -= 1j
+    m = dict(model)
+    m["h"], m["eps"], m["U"] = h, eps, U
+    return m
+
+
+def green_equilibrium_grad_dense(model, orbitals, dt, n_steps, dG_gtr=None, dG_les=None):
+    """Analytic gradient of a real loss L of the equilibrium Green's function
+    (Section 3, Eq. (psigreen) with eta = 0, and the hole part after Eq.
+    (gomega)) with respect to the Hamiltonian parameters, from the dense
+    eigen-decompositions of the sector and neighbour-sector Hamiltonians
+    (small sectors only).  The paper has no gradients; this is the plain
+    first-order perturbation theory of the Lehmann form:
+
+      G^>_{aa'}(t) = -i <0| c_a e^{-i(H_+ - E0) t} c^dag_a' |0>,
+      G^<_{aa'}(t) = +i <0| c^dag_a' e^{+i(H_- - E0) t} c_a |0>,
+
+    differentiated through three routes --
+      * the neighbour Hamiltonians H_+/-: d f(H) = Q (F o Q^dag dH Q) Q^dag
+        with F the first divided differences of f on the eigenvalues
+        (Daleckii-Krein), f(E) = e^{-/+ i (E - E0) t};
+      * E0: dE0 = <0|dH|0> (Hellmann-Feynman), dG^>/dE0 = i t G^>,
+        dG^</dE0 = -i t G^<;
+      * |0>: d|0> = sum_{n != 0} |n><n|dH|0> / (E0 - E_n).
+    The cotangents are dG = dL/dRe G + i dL/dIm G (either may be None = 0),
+    so dL = Re sum conj(dG) dG_theta.  Returns (g_eps [2, L], g_hre [L, L],
+    g_him [L, L], g_U [L]) in the convention of the library's VJP: g_hre is
+    symmetric with the diagonal dL/dh_ii, g_him antisymmetric."""
+    L = model["L"]
+    n = len(orbitals)
+    shape = (n_steps + 1, n, n)
+    A = np.zeros(shape, np.complex128) if dG_gtr is None else np.asarray(dG_gtr, np.complex128)
+    B = np.zeros(shape, np.complex128) if dG_les is None else np.asarray(dG_les, np.complex128)
+    t = dt * np.arange(n_steps + 1)
+    sec = Sector(model)
+    w0, Q0 = _eigh(dense_hamiltonian(sec))
+    if w0.size > 1 and w0[1] - w0[0] < 1e-8 * max(1.0, abs(w0[0])):
+        raise ValueError("degenerate ground state: no gradient")
+    E0, psi = w0[0], Q0[:, 0]
+    dL_dE0 = 0.0
+    w_vec = np.zeros(sec.dim, dtype=np.complex128)   # (Omega + Omega^dag)|0>
+    Y = []                                            # (sector, Y): dL = Re sum(Y * dH)
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger in (True, False):
+            nb = sec.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            E, Q = _eigh(dense_hamiltonian(nb))
+            u = np.stack([sec.apply_cop(nb, orbitals[a][0], spin, dagger, psi) for a in idx])  # [na, dn]
+            p = u @ Q.conj()                                                                    # p[a] = Q^dag u_a
+            C = np.conj(A if dagger else B)[:, idx][:, :, idx]                                 # [t, a, a']
+            sgn = -1.0 if dagger else 1.0                    # e^{sgn i (E - E0) t}
+            ph = np.exp(sgn * 1j * np.outer(t, E - E0))      # [t, m]
+            pref = -1j if dagger else 1j
+            # the Green's function block itself (for the E0 route)
+            if dagger:   # G^>_{aa'}(t) = -i sum_m conj(p_am) p_a'm ph_tm
+                G = pref * np.einsum("am,bm,tm->tab", p.conj(), p, ph)
+            else:        # G^<_{aa'}(t) = +i sum_m conj(p_a'm) p_am ph_tm
+                G = pref * np.einsum("bm,am,tm->tab", p.conj(), p, ph)
+            dL_dE0 += float(np.sum(C * (-sgn) * 1j * t[:, None, None] * G).real)
+            # g_{aa'}(E) = pref sum_t C_t,aa' e^{sgn i (E - E0) t} and its E-derivative
+            g = pref * np.einsum("tab,tm->abm", C, ph)
+            dg = pref * np.einsum("tab,tm->abm", C * (sgn * 1j * t)[:, None, None], ph)
+            Z = np.zeros((nb.dim, nb.dim), dtype=np.complex128)
+            na = len(idx)
+            for ia in range(na):
+                for ib in range(na):
+                    D = _divided_differences(g[ia, ib], dg[ia, ib], E)
+                    if dagger:   # Z_mn += conj(p_am) p_a'n D
+                        Z += np.outer(p[ia].conj(), p[ib]) * D
+                    else:        # Z_mn += conj(q_a'm) q_an D
+                        Z += np.outer(p[ib].conj(), p[ia]) * D
+            Y.append((nb, _sandwich(Q, Z)))
+            # (Omega + Omega^dag)|0>, Omega = sum C O with G = <0|O|0>
+            for ia, a in enumerate(idx):
+                for ib, b in enumerate(idx):
+                    if dagger:   # O = -i c_a e^{-i(H+ - E0)t} c^dag_b
+                        fwd = Q @ (g[ia, ib] * p[ib])                 # into c_a
+                        bwd = Q @ (np.conj(g[ia, ib]) * p[ia])        # into c_b
+                        w_vec += nb.apply_cop(sec, orbitals[a][0], spin, False, fwd)
+                        w_vec += nb.apply_cop(sec, orbitals[b][0], spin, False, bwd)
+                    else:        # O = +i c^dag_b e^{+i(H- - E0)t} c_a
+                        fwd = Q @ (g[ia, ib] * p[ia])                 # into c^dag_b
+                        bwd = Q @ (np.conj(g[ia, ib]) * p[ib])        # into c^dag_a
+                        w_vec += nb.apply_cop(sec, orbitals[b][0], spin, True, fwd)
+                        w_vec += nb.apply_cop(sec, orbitals[a][0], spin, True, bwd)
+    # the ground-state routes: R = sum_{n != 0} |n><n| / (E0 - E_n)
+    inv = np.zeros_like(w0)
+    inv[1:] = 1.0 / (E0 - w0[1:])
+    Rw = Q0 @ (inv * (Q0.conj().T @ w_vec))
+    Y.append((sec, np.outer(psi.conj(), Rw) + dL_dE0 * np.outer(psi.conj(), psi)))
+
+    diags = [(s, np.ascontiguousarray(np.diagonal(Ys).real), s.basis()) for s, Ys in Y]
+
+    def grad(kind, i, j=None):
+        tot = 0.0
+        if kind in ("eps", "U"):  # diagonal dH: the occupation n_{i sigma} or n_{i up} n_{i dn}
+            for s, yd, basis in diags:
+                if kind == "eps":
+                    occ = (basis >> np.uint64(i * L + j)) & np.uint64(1)
+                else:
+                    occ = ((basis >> np.uint64(i)) & (basis >> np.uint64(L + i))) & np.uint64(1)
+                tot += float(np.dot(yd, occ.astype(np.float64)))
+            return tot
+        for s, Ys in Y:
+            dH = dense_hamiltonian(Sector(_unit_model(model, kind, i, j), s.n_up, s.n_dn))
+            tot += float(np.sum(Ys * dH).real)
+        return tot
+
+    g_eps = np.array([[grad("eps", sg, i) for i in range(L)] for sg in range(2)])
+    g_U = np.array([grad("U", i) for i in range(L)])
+    g_hre = np.zeros((L, L))
+    g_him = np.zeros((L, L))
+    for i in range(L):
+        g_hre[i, i] = grad("re", i, i)
+        for j in range(i + 1, L):
+            g_hre[i, j] = g_hre[j, i] = grad("re", i, j)
+            g_him[i, j] = grad("im", i, j)
+            g_him[j, i] = -g_him[i, j]
+    return g_eps, g_hre, g_him, g_U
+
+
+def keldysh_entries(ini, fin, samples, dt, gs=None, K=80, tol=1e-12):
+    """Several sampled entries of the Keldysh grid at any size: for each
+    (k, l, orbital_a, orbital_b) of `samples`, the pair (G^<_{ab}(t_k,t_l),
+    G^>_{ab}(t_k,t_l)) of Section 4, steps (i)-(iv), computed exactly as
+    keldysh_entry does, with every Phi(t_k) and every back-propagated vector
+    formed once and shared between the entries that use it."""
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    sec_f = Sector(fin)
+    phi, vec, nbs = {}, {}, {}
+
+    def phi_at(k):
+        if k not in phi:
+            phi[k] = sec_f.propagate(psi0, dt * k) if k else psi0
+        return phi[k]
+
+    def back(k, orb, dagger):
+        key = (k, orb, dagger)
+        if key not in vec:
+            site, spin = orb
+            if (spin, dagger) not in nbs:
+                nbs[(spin, dagger)] = sec_f.neighbour(spin, dagger)
+            nb = nbs[(spin, dagger)]
+            vec[key] = None if nb is None else nb.propagate(sec_f.apply_cop(nb, site, spin, dagger, phi_at(k)),
+                                                            -dt * k)
+        return vec[key]
+
+    out = []
+    for (k, l, oa, ob) in samples:
+        if oa[1] != ob[1]:
+            out.append((0j, 0j))
+            continue
+        pair = []
+        for dagger in (False, True):
+            va, vb = back(k, tuple(oa), dagger), back(l, tuple(ob), dagger)
+            if va is None:
+                pair.append(0j)
+            else:
+                pair.append(1j * np.vdot(vb, va) if not dagger else -1j * np.vdot(va, vb))
+        out.append(tuple(pair))
+    return out

@@ -277,6 +277,34 @@ void ko_hpsi(const ko_model* M, const double* x, double* y) {
 
 // y = c_{site,spin} x (dagger = 0) or c^dag_{site,spin} x (dagger = 1); y lives
 // in dst's sector, which must be the neighbouring one.  Returns 0 or -1.
+// The sector Hamiltonian as a dense row-major d x d matrix: the same terms as
+// ko_hpsi, each written to its own entry H[s][k] (one hopping term links a
+// pair of states at most, so every entry is a single term or the diagonal).
+void ko_dense_h(const ko_model* M, double* out_) {
+    cd* out = reinterpret_cast<cd*>(out_);
+    const long d = (long)M->basis.size();
+    const int L = M->L;
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < d; ++s) {
+        cd* row = out + s * d;
+        for (long k = 0; k < d; ++k) row[k] = cd(0.0, 0.0);
+        const uint64_t st = M->basis[s];
+        row[s] = diag_energy(M, st);
+        for (int sg = 0; sg < 2; ++sg)
+            for (int i = 0; i < L; ++i)
+                for (int j = 0; j < L; ++j) {
+                    if (i == j) continue;
+                    const cd hij = M->h[i * L + j];
+                    if (hij == cd(0.0, 0.0)) continue;
+                    uint64_t t1, t2;
+                    double s1, s2;
+                    if (!op_c(st, sg * L + i, &t1, &s1)) continue;
+                    if (!op_cdag(t1, sg * L + j, &t2, &s2)) continue;
+                    row[find_state(M, t2)] += hij * (s1 * s2);
+                }
+    }
+}
+
 int ko_apply_cop(const ko_model* src, const ko_model* dst, int site, int spin, int dagger,
                  const double* x_, double* y_) {
     if (src->L != dst->L) return -1;

@@ -680,3 +680,121 @@ def test_keldysh_entry_matches_the_gram_route():
         for a, b in ((0, 1), (1, 0), (2, 3), (0, 2)):
             les, gtr = oracle.keldysh_entry(ini, fin, orbs[a], orbs[b], dt, k, l)
             assert abs(les - Gl[k, l, a, b]) < 1e-12 and abs(gtr - Gg[k, l, a, b]) < 1e-12, (k, l, a, b)
+
+
+# ------------------------------------------- dense analytic gradient pins
+def _dense_expm_green(model, c, orbs, dt, n):
+    """G^>(t_k), G^<(t_k) from the Jordan-Wigner Fock matrices: ground state
+    by eigh of the sector block, propagators by scipy expm of the whole Fock
+    H (powers of one step)."""
+    L = model["L"]
+    H = dense_fock_h(model, c)
+    i0 = sector_index(L, model["n_up"], model["n_dn"])
+    w, v = np.linalg.eigh(H[np.ix_(i0, i0)])
+    g = np.zeros(H.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    step = sla.expm(-1j * dt * H)
+    U_t = np.eye(H.shape[0], dtype=np.complex128)
+    no = len(orbs)
+    Gg = np.zeros((n + 1, no, no), dtype=np.complex128)
+    Gl = np.zeros_like(Gg)
+    ops = [c[s * L + i] for (i, s) in orbs]
+    for k in range(n + 1):
+        t = k * dt
+        for a in range(no):
+            for b in range(no):
+                Gg[k, a, b] = -1j * np.exp(1j * w[0] * t) * (g.conj() @ ops[a] @ U_t @ ops[b].T @ g)
+                Gl[k, a, b] = 1j * np.exp(-1j * w[0] * t) * (g.conj() @ ops[b].T @ U_t.conj().T @ ops[a] @ g)
+        U_t = step @ U_t
+    return Gg, Gl
+
+
+@pytest.mark.parametrize("seed,nu,nd", [(41, 2, 2), (42, 1, 2)])
+def test_dense_gradient_vs_expm_central_differences(seed, nu, nd):
+    """The analytic gradient (perturbation theory of the Lehmann form) against
+    central differences (step 1e-5) of the Jordan-Wigner expm forward, for
+    every parameter: eps, U, the diagonal and the real and imaginary parts of
+    every hopping pair, with random complex cotangents on both parts and
+    orbitals of both spins.  A dropped route (E0, |0>, the neighbour
+    Hamiltonians), a sign or a conjugate fails it."""
+    L = 4
+    c = jw_parts(L)
+    m = W.random_model(L, nu, nd, seed=seed, complex_hopping=True)
+    orbs = [(0, 0), (2, 0), (1, 1)]
+    dt, n = 0.15, 10
+    rng = np.random.default_rng(seed)
+    shape = (n + 1, len(orbs), len(orbs))
+    A = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    B = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    g_eps, g_hre, g_him, g_U = oracle.green_equilibrium_grad_dense(m, orbs, dt, n, A, B)
+
+    def loss(mm):
+        Gg, Gl = _dense_expm_green(mm, c, orbs, dt, n)
+        return float(np.sum((np.conj(A) * Gg).real) + np.sum((np.conj(B) * Gl).real))
+
+    def fd(kind, i, j):
+        out = []
+        for dlt in (1e-5, -1e-5):
+            mm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in m.items()}
+            if kind == "eps":
+                mm["eps"][i, j] += dlt
+            elif kind == "U":
+                mm["U"][i] += dlt
+            elif kind == "re":
+                mm["h"][i, j] += dlt
+                if i != j:
+                    mm["h"][j, i] += dlt
+            else:
+                mm["h"][i, j] += 1j * dlt
+                mm["h"][j, i] -= 1j * dlt
+            out.append(loss(mm))
+        return (out[0] - out[1]) / 2e-5
+
+    checks = [(g_eps[s, i], fd("eps", s, i)) for s in range(2) for i in range(L)]
+    checks += [(g_U[i], fd("U", i, None)) for i in range(L)]
+    checks += [(g_hre[i, j], fd("re", i, j)) for i in range(L) for j in range(i, L)]
+    checks += [(g_him[i, j], fd("im", i, j)) for i in range(L) for j in range(i + 1, L)]
+    scale = max(1.0, max(abs(r) for _, r in checks))
+    for k, (g, r) in enumerate(checks):
+        assert abs(g - r) < 1e-7 * scale, (k, g, r)
+    # the tied conventions: symmetric real part, antisymmetric imaginary part
+    assert np.array_equal(g_hre, g_hre.T) and np.array_equal(g_him, -g_him.T)
+    # the diagonal of h acts like eps on both spins
+    assert np.max(np.abs(np.diag(g_hre) - g_eps.sum(0))) < 1e-9 * scale
+
+
+def test_dense_gradient_U0_translation_and_zero_cotangent():
+    """Zero cotangents give a zero gradient; on the translation-invariant U = 0
+    ring with the loss of a site-diagonal function summed over all sites, every
+    site's eps gradient is the same (symmetry of the loss)."""
+    L = 6
+    m = W.hubbard_ring(L, 0.0, 2, 2, pbc=False)
+    m["h"] = W.ring_hopping(L, 1.0, pbc=True).astype(np.complex128)
+    m["h"][0, 1] = m["h"][1, 0] = -1.0 + 0.0j
+    # antiperiodic twist keeps the 6-ring closed-shell at (2,2)
+    m["h"][0, L - 1] = m["h"][L - 1, 0] = 1.0
+    orbs = [(i, 0) for i in range(L)]
+    dt, n = 0.1, 8
+    g0 = oracle.green_equilibrium_grad_dense(m, orbs, dt, n)
+    assert all(np.max(np.abs(x)) == 0.0 for x in g0)
+    A = np.zeros((n + 1, L, L), dtype=np.complex128)
+    for i in range(L):
+        A[:, i, i] = 1.0 + 0.5j
+    g_eps, _, _, _ = oracle.green_equilibrium_grad_dense(m, orbs, dt, n, A, A)
+    assert np.max(np.abs(g_eps[0] - g_eps[0, 0])) < 1e-9 * max(1.0, abs(g_eps[0, 0]))
+
+
+def test_keldysh_entries_share_work_and_match_single_entries():
+    """The batched sampling route gives the single-entry route's numbers (which
+    are pinned to the Gram route above) for a mix of times, orbitals and
+    spins, including a pair of opposite spins (zero)."""
+    ini = W.random_model(4, 2, 1, seed=73, complex_hopping=True)
+    fin = W.random_model(4, 2, 1, seed=74, complex_hopping=True)
+    dt = 0.25
+    samples = [(3, 0, (0, 0), (2, 0)), (1, 4, (2, 0), (0, 0)), (4, 4, (1, 1), (3, 1)), (2, 2, (0, 0), (1, 1)),
+               (0, 3, (3, 1), (3, 1))]
+    got = oracle.keldysh_entries(ini, fin, samples, dt)
+    for (k, l, a, b), (les, gtr) in zip(samples, got):
+        rl, rg = oracle.keldysh_entry(ini, fin, a, b, dt, k, l)
+        assert abs(les - rl) < 1e-13 and abs(gtr - rg) < 1e-13, (k, l, a, b)
+    assert got[3] == (0j, 0j)
