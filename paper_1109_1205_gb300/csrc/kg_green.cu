@@ -792,6 +792,7 @@ static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
 static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
     const int na = (int)B.idx.size(), dn = (int)B.nb->d;
     const double2* phik = X->phi + (size_t)k * X->fin->d;
+    KG_TRY(launch_reset_status(B.K, st));
     for (int a = 0; a < na; ++a)
         KG_TRY(launch_cop(X->fin, B.nb, X->orb[2 * B.idx[a]], B.spin, B.dagger, phik, B.K.vec(a, 0), st));
     for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));

@@ -21,6 +21,7 @@ constexpr int kChunk = 24;     // complex dot products accumulated per pass
 constexpr int kMaxOv = 32;     // overlap vectors fused into the combination pass
 constexpr int kPart = 72;      // doubles per block in a partial-sum row
 constexpr int kThreads = 256;  // threads per block of the streaming kernels
+constexpr int kMaxSub = 1 << 17;  // largest sub-step count of a step exponential
 // H*psi gathers each input component about once per hop; a launch covers a
 // group of columns whose inputs together fit in this much L2 (of 129 MB).
 constexpr long long kHpsiGroupBytes = 72ll << 20;
@@ -255,6 +256,9 @@ int prepare_step(Krylov& K, int reorth);
 int prepare_hpsi_lists(Krylov& K);
 // Sets the overlap row counter of every column.
 int launch_set_slots(Krylov& K, int value, cudaStream_t st);
+// Clears every column's status (KG_OK); the kernels only ever raise it, so a
+// non-finite value met in any step of a call stays reported until this runs.
+int launch_reset_status(Krylov& K, cudaStream_t st);
 
 // Replays the launch sequence of one propagation step, as a CUDA graph when
 // allowed (the sequence is fixed: iteration counts and early exits after a

@@ -250,8 +250,12 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(const ColDesc* desc, const
         C->scale[0] = n > 0.0 ? 1.0 / n : 0.0;
         C->emax[0] = (int)red[1];
         C->m_eff = n > 0.0 ? M : 0;
-        C->status = isfinite(n) ? KG_OK : KG_ENUMERIC;
-        if (!isfinite(n)) C->m_eff = 0;
+        // the status is sticky over the steps of one call (reset by
+        // launch_reset_status), so a non-finite column stays reported
+        if (!isfinite(n)) {
+            C->status = KG_ENUMERIC;
+            C->m_eff = 0;
+        }
     }
 }
 
@@ -705,7 +709,7 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tridiag(const ColDesc* desc,
         __syncwarp();
         ++iter;
     }
-    if (lane == 0 && iter >= max_iter) C->status = KG_ENOCONV;
+    if (lane == 0 && iter >= max_iter && C->status == KG_OK) C->status = KG_ENOCONV;
     __syncwarp();
     if (mode == 0 || mode == 2) {
         // mode 0: the column's own tau into C->c; mode 2: ntau times
@@ -846,7 +850,18 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_texp(const ColDesc* desc, Co
         }
         const double tau = tfull - tprev;
         tprev = tfull;
-        const int nsub = max(1, (int)ceil(2.0 * g * fabs(tau)));
+        // a non-finite or absurdly large T (more than kMaxSub sub-steps)
+        // cannot be exponentiated this way: report it instead of looping
+        const double want = 2.0 * g * fabs(tau);
+        if (!(want <= (double)kMaxSub)) {
+            if (lane == 0) C->status = KG_ENUMERIC;
+            for (int k = lane; k < Mcap; k += 32) C->c[k] = make_double2(0.0, 0.0);
+            if (mode == 2)
+                for (int t2 = 0; t2 < ntau; ++t2)
+                    for (int k = lane; k < Mcap; k += 32) cq[((size_t)b * ntau + t2) * Mcap + k] = make_double2(0.0, 0.0);
+            return;
+        }
+        const int nsub = max(1, (int)ceil(want));
         const double h = tau / nsub;
         for (int sub = 0; sub < nsub; ++sub) {
             double2 term[R], sum[R], y[R];
@@ -1097,6 +1112,17 @@ int launch_tridiag_multi(Krylov& K, const double* taus, int ntau, double2* cq, c
 // -------------------------------------------------- step sequencing
 __global__ void k_set_slots(ColScalars* cs, int B, int value) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) cs[b].ov_slot = value;
+}
+
+__global__ void k_reset_status(ColScalars* cs, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) cs[b].status = KG_OK;
+}
+
+int launch_reset_status(Krylov& K, cudaStream_t st) {
+    k_reset_status<<<(K.B + 127) / 128, 128, 0, st>>>(K.cs, K.B);
+    KG_LAUNCHED();
+    return KG_OK;
 }
 
 int launch_set_slots(Krylov& K, int value, cudaStream_t st) {

@@ -225,6 +225,16 @@ int sector_build(int L, int nu, int nd, const double* h_re, const double* h_im, 
         set_error("invalid sector (L=%d, n_up=%d, n_dn=%d) or NULL parameter array", L, nu, nd);
         return KG_EINVAL;
     }
+    for (int k = 0; k < L * L; ++k)
+        if (!std::isfinite(h_re[k]) || (h_im && !std::isfinite(h_im[k]))) {
+            set_error("hopping element %d is not finite", k);
+            return KG_EINVAL;
+        }
+    for (int k = 0; k < 2 * L; ++k)
+        if (!std::isfinite(eps[k]) || (k < L && !std::isfinite(U[k]))) {
+            set_error("eps or U element %d is not finite", k);
+            return KG_EINVAL;
+        }
     double hmax = 0.0;
     for (int k = 0; k < L * L; ++k) hmax = fmax(hmax, fabs(h_re[k]) + (h_im ? fabs(h_im[k]) : 0.0));
     for (int i = 0; i < L; ++i)

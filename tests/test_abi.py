@@ -78,6 +78,17 @@ def test_argument_validation_before_device_use(kg):
     hr = np.array([[0.0, 1.0], [1.0, 0.0]])
     rc = lib.kg_build_sector(2, 1, 1, hr.ctypes.data, hi.ctypes.data, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
     assert rc == kg.KG_EINVAL
+    # non-finite parameters (a NaN also passes a Hermiticity comparison, so it
+    # is rejected on its own)
+    for bad_h, bad_e, bad_u in [(np.nan, 0.0, 0.0), (np.inf, 0.0, 0.0), (0.0, np.nan, 0.0), (0.0, 0.0, -np.inf)]:
+        hh = np.array([[0.0, bad_h], [bad_h, 0.0]])
+        ee = np.full(4, bad_e)
+        uu = np.full(2, bad_u)
+        rc = lib.kg_build_sector(2, 1, 1, hh.ctypes.data, None, ee.ctypes.data, uu.ctypes.data, ctypes.byref(out))
+        assert rc == kg.KG_EINVAL and "not finite" in kg.kg_last_error()
+    hi = np.array([[0.0, np.nan], [-np.nan, 0.0]])
+    rc = lib.kg_build_sector(2, 1, 1, hr.ctypes.data, hi.ctypes.data, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
+    assert rc == kg.KG_EINVAL
     # dimension beyond 2^31
     big = np.zeros(32 * 32)
     rc = lib.kg_build_sector(32, 16, 16, big.ctypes.data, None, z.ctypes.data, z.ctypes.data, ctypes.byref(out))
