@@ -310,7 +310,11 @@ int kg_green_equilibrium_batched(kg_sector* const* s, int n_inst, const int* orb
  *   g_eps[sigma*L + i] = dL/d eps_{i sigma},     g_U[i] = dL/dU_i,
  *   g_hre[i*L + j] = dL/dRe h_ij  (h_ji = conj(h_ij) tied, so symmetric;
  *                    the diagonal is dL/dh_ii = sum over spins of g_eps),
- *   g_him[i*L + j] = dL/dIm h_ij  (antisymmetric).
+ *   g_him[i*L + j] = dL/dIm h_ij  (antisymmetric),
+ * for the bonds of the model (pairs i != j with h_ij != 0, whose hops the
+ * sector tables hold) and the diagonal; entries of pairs absent from the
+ * model are returned as zero (a caller that needs the derivative with respect
+ * to a new bond passes that bond with a tiny nonzero amplitude).
  * Method: adjoint states propagated backward with the same Krylov steps,
  * Frechet derivative of each step by 10-point Gauss-Legendre quadrature with
  * node vectors from that step's Krylov spaces, ground-state terms by

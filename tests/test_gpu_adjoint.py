@@ -1,10 +1,17 @@
 """The adjoint of the equilibrium Green's function.
 
-The library's vector-Jacobian product is checked against central finite
-differences (h = 1e-6) of the CPU oracle's forward (an independent Chebyshev
-propagation) on small models with every cotangent path active, and at the
-full size of the bath-fitting workload (star SIAM L = 10, (5,5), 401 times,
-checkpoints every 20 steps) against central differences of the GPU forward.
+The library's vector-Jacobian product is checked against
+* the oracle's analytic gradient (first-order perturbation theory of the
+  Lehmann form from dense eigen-decompositions) on the bath-fitting star at
+  L = 6 and L = 8 (d = 400 and 4,900, 401 times) and on a complex-hopping
+  model, to 1e-8 relative;
+* central finite differences (h = 1e-6) of the CPU oracle's forward (an
+  independent Chebyshev propagation) on small models with every cotangent
+  path active;
+* at the full size of the bath-fitting workload (star SIAM L = 10, (5,5),
+  d = 63,504): central differences of the oracle's forward on a short grid,
+  and central differences of the GPU forward on all 401 times (checkpoints
+  every 20 steps).
 """
 import math
 
@@ -197,3 +204,115 @@ def test_c5_full_size_vs_gpu_fd():
             return mm
         ref = (gpu_loss(pert(h))[0] - gpu_loss(pert(-h))[0]) / (2 * h)
         assert abs(g - ref) <= 2e-5 * max(1.0, abs(ref)), (kind, k, g, ref)
+
+
+# ------------------------------------------- the dense-oracle gradient
+def _compare(got, ref, tol, model):
+    """All eps and U gradients, and the hopping gradients of the model's bonds
+    and the diagonal (the library returns zero for pairs absent from the
+    model, which the oracle differentiates too)."""
+    bonds = (model["h"] != 0) | np.eye(model["L"], dtype=bool)
+    ref = (ref[0], np.where(bonds, ref[1], 0.0), np.where(bonds, ref[2], 0.0), ref[3])
+    scale = max(1.0, max(float(np.max(np.abs(r))) for r in ref))
+    for name, g, r in zip(("eps", "hre", "him", "U"), got, ref):
+        assert np.max(np.abs(np.asarray(g) - r)) <= tol * scale, (name, np.max(np.abs(np.asarray(g) - r)), scale)
+
+
+@pytest.mark.parametrize("L", [6, 8])
+def test_vjp_vs_dense_oracle_gradient_bath_fit(L):
+    """The bath-fitting gradient of the adjoint workload's star model (401
+    times, checkpoints every 20 steps) at L = 6 (d = 400) and L = 8 (d = 4,900)
+    against the oracle's analytic gradient, every parameter (eps of both spins,
+    U, every hopping pair's real and imaginary part)."""
+    dt, n = 0.05, 400
+    tgt, *_ = c5_like(L, 7)
+    m, *_ = c5_like(L, 8)
+    orbs = [(0, 0)]
+    Tg, Tl, _ = oracle.green_equilibrium(tgt, orbs, dt, n, K=120, tol=1e-14)
+    Gg, Gl, _ = oracle.green_equilibrium(m, orbs, dt, n, K=120, tol=1e-14)
+    r = 2.0 * ((Gg - Gl) - (Tg - Tl))
+    ref = oracle.green_equilibrium_grad_dense(m, orbs, dt, n, r, -r)
+    s = kg.Sector(m)
+    got = kg.kg_green_equilibrium_vjp(s.handle, L, orbs, dt, n, r, -r, checkpoint=20)
+    _compare(got, ref, 1e-8, m)
+
+
+def test_vjp_vs_dense_oracle_gradient_complex_two_spins():
+    """Random complex cotangents on both parts, orbitals of both spins and a
+    complex Hermitian hopping matrix with some bonds absent (d = 300, 200
+    times)."""
+    m = W.random_model(6, 3, 2, seed=44, complex_hopping=True, density=0.7)
+    orbs = [(0, 0), (3, 0), (2, 1)]
+    dt, n = 0.05, 200
+    rng = np.random.default_rng(45)
+    shape = (n + 1, len(orbs), len(orbs))
+    A = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    B = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    ref = oracle.green_equilibrium_grad_dense(m, orbs, dt, n, A, B)
+    s = kg.Sector(m)
+    got = kg.kg_green_equilibrium_vjp(s.handle, 6, orbs, dt, n, A, B, checkpoint=13)
+    _compare(got, ref, 1e-8, m)
+
+
+def test_c5_full_size_vs_oracle_fd():
+    """The full-size bath-fitting sector (d = 63,504) on a short grid (41
+    times): the adjoint against central differences of the oracle's forward
+    in U, one eps_k and one V_k.  Step 1e-4: the oracle's ground state is
+    converged to a residual of 1e-14, which leaves ~1e-12 of noise in the
+    loss, 1e-8 after the division; the truncation error is ~1e-8."""
+    cfg = W.config_c5()
+    L, dt, n, orbs = 10, cfg["dt"], 40, cfg["orbitals"]
+    h = 1e-4
+    Tg, Tl, _ = oracle.green_equilibrium(cfg["target"], orbs, dt, n, K=80, tol=1e-14)
+    T = (Tg - Tl)[:, 0, 0]
+    m = cfg["start"]
+
+    def loss(model):
+        Gg, Gl, _ = oracle.green_equilibrium(model, orbs, dt, n, K=80, tol=1e-14)
+        return float(np.sum(np.abs((Gg - Gl)[:, 0, 0] - T) ** 2)), Gg, Gl
+
+    _, Gg, Gl = loss(m)
+    r = 2.0 * ((Gg - Gl)[:, 0, 0] - T)
+    dGg = np.zeros_like(Gg)
+    dGl = np.zeros_like(Gl)
+    dGg[:, 0, 0] = r
+    dGl[:, 0, 0] = -r
+    s = kg.Sector(m)
+    opts = kg.kg_opts_default(M=cfg["M"], tol_resid=1e-14, max_restarts=1000)
+    g_eps, g_hre, _, g_U = kg.kg_green_equilibrium_vjp(s.handle, L, orbs, dt, n, dGg, dGl, opts, checkpoint=20)
+    for kind, k, g in (("U", 0, g_U[0]), ("e", 4, g_eps[0, 4] + g_eps[1, 4]), ("v", 7, g_hre[0, 7])):
+        def pert(delta):
+            mm = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in m.items()}
+            if kind == "U":
+                mm["U"][0] += delta
+            elif kind == "e":
+                mm["eps"][:, k] += delta
+            else:
+                mm["h"][0, k] += delta
+                mm["h"][k, 0] += delta
+            return mm
+        ref = (loss(pert(h))[0] - loss(pert(-h))[0]) / (2 * h)
+        assert abs(g - ref) <= 2e-6 * max(1.0, abs(ref)), (kind, k, g, ref)
+
+
+def test_autograd_frees_the_sector_without_backward(monkeypatch):
+    """A forward whose graph is dropped without a backward releases its sector
+    handle; CUDA inputs give CUDA outputs."""
+    import gc
+
+    from paper_1109_1205_gb300 import _lib
+    freed = []
+    orig = _lib.kg_free_sector
+    monkeypatch.setattr(_lib, "kg_free_sector", lambda hdl: (freed.append(hdl), orig(hdl))[1])
+    m = W.siam_star(-1.5, 3.0, [-1.0, 0.3, 1.2], [0.5, 0.7, 0.4], 2, 2)
+    h = torch.tensor(m["h"].real, device="cuda", requires_grad=True)
+    eps = torch.tensor(m["eps"], device="cuda")
+    Uv = torch.tensor(m["U"], device="cuda")
+    Gg, Gl = green_equilibrium(h, eps, Uv, 4, 2, 2, [(0, 0)], 0.1, 5)
+    assert Gg.is_cuda and Gl.is_cuda
+    del Gg, Gl
+    gc.collect()
+    assert len(freed) == 1
+    Gg, Gl = green_equilibrium(h, eps, Uv, 4, 2, 2, [(0, 0)], 0.1, 5)
+    (Gg.abs().sum() + Gl.abs().sum()).backward()
+    assert len(freed) == 2 and h.grad is not None and h.grad.is_cuda
