@@ -420,28 +420,82 @@ def test_keldysh_mismatched_sectors():
     assert e.value.code == kg.KG_EINVAL
 
 
-# ------------------------------------------- full-size c2, sampled entries
-def test_c2_full_size_sampled():
-    """The Hubbard-ring quench at its full size (d = 853,776), in the launch
-    configuration of the benchmark: E0 of H_ini, and sampled entries of the
-    time-diagonal blocks G(t_k, t_k) against the oracle computed one by one."""
+# ------------------------------------------------ full-size c2, whole grid
+C2_SAMPLES = ([(k, k, 0, b) for k in (0, 3, 40, 99) for b in (0, 5)]
+              + [(99, 0, 0, 0), (99, 0, 0, 5), (60, 20, 0, 0), (60, 20, 0, 5), (20, 60, 5, 0)])
+
+
+@pytest.fixture(scope="module")
+def c2_grid():
+    """The Hubbard-ring quench at its full size (d = 853,776; columns in the
+    N-1 / N+1 sectors, d = 731,808), in the launch configuration of the
+    benchmark: every row of step (iii) through the staged API (the call the
+    benchmark times), then the step-(iv) Gram of 1,200 vectors per part.  The
+    oracle's ground state and sampled entries are computed on the host cores
+    meanwhile (the library calls release the interpreter)."""
+    from concurrent.futures import ThreadPoolExecutor
     cfg = W.config_c2()
-    si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
-    opts = kg.kg_opts_default(M=cfg["M"])
-    E0, res, _ = si.ground_state(opts)
-    osec = oracle.Sector(cfg["ini"])
-    e_or, psi_or, _ = osec.ground_state()
-    assert abs(E0 - e_or) <= E_TOL * abs(e_or)
-    K = kg.Keldysh(si, sf, cfg["orbitals"], cfg["dt"], cfg["n_t"], opts)
-    for k in (0, 3):
-        dl, dg = K.row(k)
-        for (a, b) in ((0, 0), (0, 5)):
-            les, gtr = oracle.keldysh_entry(cfg["ini"], cfg["fin"], cfg["orbitals"][a], cfg["orbitals"][b],
-                                            cfg["dt"], k, k, gs=(e_or, psi_or, 0.0))
-            assert abs(dl[a, b] - les) < G_TOL and abs(dg[a, b] - gtr) < G_TOL, (k, a, b)
-        # half filling + particle-hole symmetry of the ring: n_i(t) = 1/2
-        assert np.max(np.abs((-1j * np.diag(dl)).real - 0.5)) < 1e-10
-    K.close()
+    orbs = cfg["orbitals"]
+
+    def oracle_side():
+        e_or, psi_or, _ = oracle.Sector(cfg["ini"]).ground_state()
+        samples = [(k, l, orbs[a], orbs[b]) for (k, l, a, b) in C2_SAMPLES]
+        return e_or, oracle.keldysh_entries(cfg["ini"], cfg["fin"], samples, cfg["dt"], gs=(e_or, psi_or, 0.0))
+
+    with ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle_side)
+        si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+        opts = kg.kg_opts_default(M=cfg["M"])
+        E0, _, _ = si.ground_state(opts)
+        K = kg.Keldysh(si, sf, orbs, cfg["dt"], cfg["n_t"], opts)
+        diag = [K.row(k) for k in range(cfg["n_t"])]
+        Gl, Gg = K.gram()
+        K.close()
+        e_or, entries = fut.result()
+    return {"E0": E0, "e_or": e_or, "diag": diag, "Gl": Gl, "Gg": Gg, "entries": entries}
+
+
+def test_c2_ground_state_full_size(c2_grid):
+    assert abs(c2_grid["E0"] - c2_grid["e_or"]) <= E_TOL * abs(c2_grid["e_or"])
+
+
+def test_c2_rows_at_depth_vs_oracle(c2_grid):
+    """Time-diagonal blocks returned by the rows themselves (99 backward
+    G-steps per column at k = 99, the benchmarked row) against the oracle."""
+    for (k, l, a, b), (les, gtr) in zip(C2_SAMPLES, c2_grid["entries"]):
+        if k != l:
+            continue
+        dl, dg = c2_grid["diag"][k]
+        assert abs(dl[a, b] - les) < G_TOL and abs(dg[a, b] - gtr) < G_TOL, (k, a, b)
+
+
+def test_c2_gram_off_diagonal_vs_oracle(c2_grid):
+    """Entries of the full-size step-(iv) Gram off the time diagonal."""
+    Gl, Gg = c2_grid["Gl"], c2_grid["Gg"]
+    for (k, l, a, b), (les, gtr) in zip(C2_SAMPLES, c2_grid["entries"]):
+        assert abs(Gl[k, l, a, b] - les) < G_TOL and abs(Gg[k, l, a, b] - gtr) < G_TOL, (k, l, a, b)
+    # the Gram's diagonal blocks are the rows' own blocks
+    for k in range(Gl.shape[0]):
+        dl, dg = c2_grid["diag"][k]
+        assert np.max(np.abs(Gl[k, k] - dl)) < 1e-12 and np.max(np.abs(Gg[k, k] - dg)) < 1e-12, k
+
+
+def test_c2_whole_grid_invariants(c2_grid):
+    """Properties of every entry of the 100 x 100 x 12 x 12 grid: hermiticity
+    G(t,t')_{ab}^* = -G(t',t)_{ba}, the sum rule i(G^> - G^<)(t,t) = 1 (and 0
+    off the orbital diagonal), half filling n_i(t) = 1/2 from particle-hole
+    symmetry, and the ring's translation invariance G_{ab} = G_{a+1,b+1}."""
+    Gl, Gg = c2_grid["Gl"], c2_grid["Gg"]
+    n = Gl.shape[2]
+    for G in (Gl, Gg):
+        assert np.max(np.abs(np.conj(G) + G.transpose(1, 0, 3, 2))) < 1e-12
+        rolled = np.roll(np.roll(G, 1, axis=2), 1, axis=3)
+        assert np.max(np.abs(rolled - G)) < G_TOL
+    t = np.arange(Gl.shape[0])
+    eq_l, eq_g = Gl[t, t], Gg[t, t]
+    assert np.max(np.abs(1j * (eq_g - eq_l) - np.eye(n)[None])) < G_TOL
+    occ = (-1j * np.diagonal(eq_l, axis1=1, axis2=2)).real
+    assert np.max(np.abs(occ - 0.5)) < G_TOL
 
 
 # ------------------------------------- Lanczos G(omega), Eq. (gapprox)
