@@ -70,7 +70,8 @@ typedef struct kg_opts {
     int reorth;         /* 0: three-term recurrence only; 1: plus one full
                            Gram-Schmidt pass against every stored Lanczos
                            vector; 2: plus two passes (1)                       */
-    int batch;          /* columns per batched propagation launch, 0 = all (0) */
+    int mem_budget_mb;  /* device memory, in MiB, that a Keldysh calculation
+                           may plan for; 0 = the free memory at creation (0) */
     int schedule;       /* bit 0: H*psi hop sums in FP64 always, instead of
                            exact 64-bit integer sums when all hops share one
                            amplitude; bit 1: each propagation step's
@@ -341,16 +342,31 @@ int kg_green_keldysh(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_o
 
 /* The same computation in stages, so that a caller can schedule the rows of
  * step (iii) itself.  kg_keldysh_create runs steps (i) and (ii) and keeps
- * Phi(t_k) for all k on the device.  kg_keldysh_row runs step (iii) for one
- * time index k -- every Psi_a(t_k) and chi_a(t_k) of the orbital list,
- * batched -- stores them, and writes the time-diagonal block G(t_k, t_k)
- * (host, complex [n_orb][n_orb] each; either pointer may be NULL).
- * kg_keldysh_gram runs step (iv) over all stored rows (rows never computed
- * give KG_EINVAL) into arrays shaped like kg_green_keldysh's. */
+ * Phi(t_k) for all k.  kg_keldysh_row runs step (iii) for one time index k
+ * -- every Psi_a(t_k) and chi_a(t_k) of the orbital list, batched -- stores
+ * them, and writes the time-diagonal block G(t_k, t_k) (host, complex
+ * [n_orb][n_orb] each; either pointer may be NULL).  kg_keldysh_gram runs
+ * step (iv) over all stored rows (rows never computed give KG_EINVAL) into
+ * arrays shaped like kg_green_keldysh's.
+ *
+ * Memory plan (decided at creation against opts->mem_budget_mb, or the free
+ * device memory): Phi(t_k) stays on the device when it fits beside the
+ * largest (spin, kind) block's columns and Krylov workspace, else it is kept
+ * in host memory (pinned when possible) and one Phi(t_k) at a time is copied
+ * to the device.  When the columns of all blocks do not fit together, rows
+ * still return their time-diagonal blocks but keep no columns, and
+ * kg_keldysh_gram returns KG_EINVAL: kg_green_keldysh then computes the whole
+ * grid one block at a time (one block's columns and workspace resident).
+ * The Krylov workspaces drop their Gram-Schmidt planes (same results, slower)
+ * when the planes do not fit.  kg_keldysh_plan reports the decisions:
+ * phi_on_host 0 (device), 1 (pinned host) or 2 (pageable host); stores_kept
+ * 1 when kg_keldysh_gram is available; planes 1 when the staged rows use
+ * them; budget the byte budget planned against (any pointer may be NULL). */
 int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt,
                       int n_t, const kg_opts* o, kg_keldysh** out);
 int kg_keldysh_row(kg_keldysh* K, int k, double* G_les_kk, double* G_gtr_kk);
 int kg_keldysh_gram(kg_keldysh* K, double* G_les, double* G_gtr);
+int kg_keldysh_plan(const kg_keldysh* K, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
 /* Host copy of Phi(t_k) (complex, dimension d), and the reverse: replaces
  * the stored Phi(t_k) by a host vector (used to time a row end to end). */
 int kg_keldysh_get_phi(kg_keldysh* K, int k, double* phi_host);

@@ -14,7 +14,7 @@ from ._lib import (  # noqa: F401
     kg_free_sector, kg_sector_dims, kg_sector_strings, kg_hpsi, kg_neighbour_dim, kg_apply_cop,
     kg_ground_state, kg_copy_ground_state, kg_propagate, kg_green_equilibrium, kg_green_keldysh,
     kg_keldysh_create, kg_keldysh_row, kg_keldysh_gram, kg_keldysh_get_phi, kg_keldysh_set_phi,
-    kg_keldysh_free, kg_strerror, kg_last_error, kg_launch_count, kg_profile_start, kg_profile_stop,
+    kg_keldysh_free, kg_keldysh_plan, kg_strerror, kg_last_error, kg_launch_count, kg_profile_start, kg_profile_stop,
     kg_probe_fp64, kg_overlaps, kg_green_equilibrium_batched, kg_green_equilibrium_vjp, kg_green_lanczos,
     kg_green_equilibrium_fine, kg_green_fourier, kg_overlaps_noalloc, kg_green_matsubara,
     kg_green_matsubara_steps,

@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
         ("max_restarts", ctypes.c_int),
         ("tol_resid", ctypes.c_double),
         ("reorth", ctypes.c_int),
-        ("batch", ctypes.c_int),
+        ("mem_budget_mb", ctypes.c_int),
         ("schedule", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("dt_internal", ctypes.c_double),
@@ -75,6 +75,8 @@ _sig = {
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
+    "kg_keldysh_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(_LL)]),
     "kg_keldysh_get_phi": (_I, [_P, _I, _P]),
     "kg_keldysh_set_phi": (_I, [_P, _I, _P]),
     "kg_keldysh_free": (None, [_P]),
@@ -366,6 +368,15 @@ def kg_keldysh_gram(handle, n_t, n_orb):
     return Gl, Gg
 
 
+def kg_keldysh_plan(handle):
+    """The Keldysh memory plan: dict with phi_on_host (0 device, 1 pinned host,
+    2 pageable host), stores_kept, planes and budget (bytes)."""
+    a, b, c, d = _I(), _I(), _I(), _LL()
+    _check(lib.kg_keldysh_plan(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "kg_keldysh_plan")
+    return {"phi_on_host": a.value, "stores_kept": b.value, "planes": c.value, "budget": d.value}
+
+
 def kg_keldysh_get_phi(handle, k, out):
     _check(lib.kg_keldysh_get_phi(handle, int(k), _addr(out)), "kg_keldysh_get_phi")
     return out
@@ -502,6 +513,9 @@ class Keldysh:
 
     def gram(self):
         return kg_keldysh_gram(self.handle, self.n_t, self.n_orb)
+
+    def plan(self):
+        return kg_keldysh_plan(self.handle)
 
     def get_phi(self, k):
         out = np.empty(self.fin.dim, dtype=np.complex128)

@@ -66,7 +66,7 @@ void kg_opts_default(kg_opts* o) {
     o->max_restarts = 200;
     o->tol_resid = 1e-12;
     o->reorth = 1;
-    o->batch = 0;
+    o->mem_budget_mb = 0;
     o->schedule = 0;
     o->use_graphs = 1;
     o->dt_internal = 0.0;
@@ -224,6 +224,14 @@ int kg_keldysh_gram(kg_keldysh* K, double* G_les, double* G_gtr) {
         return KG_EINVAL;
     }
     return keldysh_gram(K, G_les, G_gtr);
+}
+
+int kg_keldysh_plan(const kg_keldysh* K, int* phi_on_host, int* stores_kept, int* planes, long long* budget) {
+    if (!K) {
+        set_error("NULL Keldysh handle");
+        return KG_EINVAL;
+    }
+    return keldysh_plan(K, phi_on_host, stores_kept, planes, budget);
 }
 
 int kg_keldysh_get_phi(kg_keldysh* K, int k, double* phi_host) {

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -740,11 +741,27 @@ int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, do
 }  // namespace kg
 
 // ------------------------------------------------------------- Keldysh
+// Memory plan.  The vectors of the four-step method can exceed the device:
+// for the 16-site chain of the local-excitation quench (d = 130.9M) Phi(t_k)
+// for 50 times is 105 GB, one (spin, kind) block of stored columns up to
+// 118 GB and one column's Krylov workspace 106 GB (57 GB without the
+// Gram-Schmidt planes).  keldysh_create therefore plans against a budget (the
+// free device memory, or opts.mem_budget_mb):
+//   * Phi(t_k) for all k stays on the device when it fits beside the blocks'
+//     needs, else in host memory (pinned when the host allows), one time
+//     staged onto the device per row;
+//   * every block keeps its Krylov workspace between rows when all fit, else
+//     each block's workspace lives only for its part of a row;
+//   * the staged API keeps every block's columns for step (iv) when they fit
+//     together; otherwise rows return their time-diagonal blocks only and
+//     the whole grid comes from kg_green_keldysh, which runs one block at a
+//     time (its columns and its workspace, with the planes when they fit).
 struct KBlock {
     int spin = 0, dagger = 0;
     std::vector<int> idx;
     kg_sector* nb = nullptr;
-    double2* store = nullptr;  // [n_t][na][d_nb]
+    double2* store = nullptr;  // [slots][na][d_nb]: every row, or only the current one
+    int slots = 0;
     double2* ovbuf = nullptr;  // [na][na]
     kg::Krylov K;
     kg::StepRunner R;
@@ -758,45 +775,92 @@ struct kg_keldysh {
     int n_orb = 0, n_t = 0, n_sub = 1;
     double dt = 0.0;
     kg_opts o;
-    double2* phi = nullptr;  // [n_t][d]
+    double2* phi = nullptr;       // [n_t][d] on the device, or
+    double2* phi_host = nullptr;  // [n_t][d] in host memory
+    bool phi_pinned = false;
+    double2* phi_stage = nullptr; // [d] device copy of one Phi(t_k) (host placement)
+    int staged = -1;              // which k phi_stage holds
+    bool keep_stores = true;      // staged API: all blocks' columns kept for step (iv)
+    bool keep_krylov = true;      // staged API: workspaces kept between rows
+    bool planes = true;           // staged API: Gram-Schmidt planes in the workspaces
+    size_t budget = 0;
     std::vector<KBlock> blocks;
     std::vector<char> row_done;
 };
 
 namespace kg {
 
-static void block_release(KBlock& B) {
+static void block_release_krylov(KBlock& B) {
     B.R.release();
     krylov_free(B.K);
+    B.ready = false;
+}
+
+static void block_release(KBlock& B) {
+    block_release_krylov(B);
     cudaFree(B.store);
     cudaFree(B.ovbuf);
     B.store = nullptr;
     B.ovbuf = nullptr;
-    B.ready = false;
+    B.slots = 0;
 }
 
-static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st) {
-    if (B.ready) return KG_OK;
+static std::vector<const kg_sector*> block_cols(const KBlock& B) {
+    return std::vector<const kg_sector*>(B.idx.size(), B.nb);
+}
+
+// Workspace (with `planes`) and `slots` rows of stored columns for block B.
+static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st, int slots, bool planes) {
     const int na = (int)B.idx.size(), dn = (int)B.nb->d;
-    std::vector<const kg_sector*> cols(na, B.nb);
-    KG_TRY(krylov_alloc(B.K, cols, std::min(X->o.M, dn), X->fin->nsm, X->o.schedule));
+    if (!B.store || B.slots != slots) {
+        cudaFree(B.store);
+        B.store = nullptr;
+        B.slots = 0;
+        if (cudaMalloc(&B.store, sizeof(double2) * (size_t)slots * na * dn) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot hold %d rows of %d columns of dimension %d", slots, na, dn);
+            return KG_ENOMEM;
+        }
+        B.slots = slots;
+    }
+    if (!B.ovbuf) KG_CUDA(cudaMalloc(&B.ovbuf, sizeof(double2) * (size_t)na * na));
+    if (B.ready) return KG_OK;
+    KG_TRY(krylov_alloc(B.K, block_cols(B), std::min(X->o.M, dn), X->fin->nsm, X->o.schedule, planes));
     for (auto& D : B.K.hdesc) D.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
     KG_TRY(krylov_upload(B.K, st));
-    KG_CUDA(cudaMalloc(&B.store, sizeof(double2) * (size_t)X->n_t * na * dn));
-    KG_CUDA(cudaMalloc(&B.ovbuf, sizeof(double2) * (size_t)na * na));
     KG_TRY(B.R.init(B.K, X->o.reorth, st, X->o.use_graphs != 0));
     B.ready = true;
     return KG_OK;
 }
 
+// Phi(t_k) on the device (staged from host memory when it lives there).
+static int phi_at(kg_keldysh* X, int k, cudaStream_t st, const double2** out) {
+    const size_t d = (size_t)X->fin->d;
+    if (X->phi) {
+        *out = X->phi + (size_t)k * d;
+        return KG_OK;
+    }
+    if (X->staged != k) {
+        KG_CUDA(cudaMemcpyAsync(X->phi_stage, X->phi_host + (size_t)k * d, sizeof(double2) * d,
+                                cudaMemcpyHostToDevice, st));
+        X->staged = k;
+    }
+    *out = X->phi_stage;
+    return KG_OK;
+}
+
+// Step (iii) for row k of block B: the columns c_a Phi(t_k) (or c^dag_a),
+// propagated back by t_k, left in slot (k or 0) of the block's store.
 static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
     const int na = (int)B.idx.size(), dn = (int)B.nb->d;
-    const double2* phik = X->phi + (size_t)k * X->fin->d;
+    const double2* phik = nullptr;
+    KG_TRY(phi_at(X, k, st, &phik));
     KG_TRY(launch_reset_status(B.K, st));
     for (int a = 0; a < na; ++a)
         KG_TRY(launch_cop(X->fin, B.nb, X->orb[2 * B.idx[a]], B.spin, B.dagger, phik, B.K.vec(a, 0), st));
     for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));
-    KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)k * na * dn, (size_t)dn * sizeof(double2), B.K.vec(0, 0),
+    const int slot = B.slots > 1 ? k : 0;
+    KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)slot * na * dn, (size_t)dn * sizeof(double2), B.K.vec(0, 0),
                               (size_t)(B.K.M + 1) * dn * sizeof(double2), (size_t)dn * sizeof(double2), na,
                               cudaMemcpyDeviceToDevice, st));
     return KG_OK;
@@ -831,6 +895,39 @@ static void block_assemble(kg_keldysh* X, KBlock& B, const std::vector<std::comp
                 }
 }
 
+static size_t device_budget(const kg_opts* o) {
+    if (o->mem_budget_mb > 0) return (size_t)o->mem_budget_mb << 20;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    const size_t reserve = std::max<size_t>(size_t(1) << 30, total_b / 32);
+    return free_b > reserve ? free_b - reserve : 0;
+}
+
+// The staged API's plan (see the comment above KBlock); Phi's placement is
+// decided before, together with its propagation's workspace.
+static void plan_blocks(kg_keldysh* X) {
+    const size_t d16 = (size_t)X->fin->d * sizeof(double2);
+    const size_t phi_dev = X->phi ? (size_t)X->n_t * d16 : d16;
+    size_t sum_store = 0, sum_kry = 0, max_kry = 0, max_kry_np = 0;
+    for (auto& B : X->blocks) {
+        const auto cols = block_cols(B);
+        const int M = std::min(X->o.M, (int)B.nb->d);
+        sum_store += (size_t)X->n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2);
+        sum_kry += krylov_bytes(cols, M, true);
+        max_kry = std::max(max_kry, krylov_bytes(cols, M, true));
+        max_kry_np = std::max(max_kry_np, krylov_bytes(cols, M, false));
+    }
+    const size_t B = X->budget;
+    X->planes = true;
+    X->keep_krylov = phi_dev + sum_store + sum_kry <= B;
+    X->keep_stores = X->keep_krylov || phi_dev + sum_store + max_kry <= B;
+    if (!X->keep_stores && phi_dev + sum_store + max_kry_np <= B) {
+        X->keep_stores = true;
+        X->planes = false;
+    }
+    if (!X->keep_stores) X->planes = phi_dev + max_kry <= B;
+}
+
 int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                    const kg_opts* o, kg_keldysh** out) {
     *out = nullptr;
@@ -840,8 +937,8 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
     }
     KG_TRY(check_orbitals(fin, orb, n_orb));
     KG_TRY(check_opts(o));
-    if (n_t < 1 || !(dt >= 0.0)) {
-        set_error("bad time grid");
+    if (n_t < 1 || !(dt >= 0.0) || o->mem_budget_mb < 0) {
+        set_error("bad time grid or memory budget");
         return KG_EINVAL;
     }
     KG_TRY(ensure_gs(ini, o));
@@ -860,40 +957,6 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
         keldysh_free(X);
         return r;
     };
-    const size_t d = (size_t)fin->d;
-    if (cudaMalloc(&X->phi, sizeof(double2) * n_t * d) != cudaSuccess) {
-        set_error("cannot hold Phi(t_k) for %d times", n_t);
-        return fail(KG_ENOMEM);
-    }
-    // step (ii): Phi(t_k) = e^{-iH t_k} |0>, stored on the grid
-    if (cudaMemcpyAsync(X->phi, ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-        return fail(KG_ECUDA);
-    if (n_t > 1) {
-        Krylov K;
-        StepRunner R;
-        int rc = krylov_alloc(K, {fin}, std::min(o->M, (int)d), fin->nsm, o->schedule);
-        if (rc == KG_OK) {
-            K.hdesc[0].tau = dt / X->n_sub;
-            rc = krylov_upload(K, st);
-        }
-        if (rc == KG_OK)
-            rc = cudaMemcpyAsync(K.vec(0, 0), ini->gs, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) == cudaSuccess
-                     ? KG_OK
-                     : KG_ECUDA;
-        if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
-        for (int k = 1; rc == KG_OK && k < n_t; ++k) {
-            for (int n = 0; rc == KG_OK && n < X->n_sub; ++n) rc = R.run(st);
-            if (rc == KG_OK)
-                rc = cudaMemcpyAsync(X->phi + k * d, K.vec(0, 0), sizeof(double2) * d, cudaMemcpyDeviceToDevice,
-                                     st) == cudaSuccess
-                         ? KG_OK
-                         : KG_ECUDA;
-        }
-        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
-        R.release();
-        krylov_free(K);
-        if (rc != KG_OK) return fail(rc);
-    }
     std::vector<int> idx[2];
     groups(orb, n_orb, idx);
     for (int spin = 0; spin < 2; ++spin) {
@@ -909,6 +972,71 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
             X->blocks.push_back(std::move(B));
         }
     }
+    // Phi's placement: on the device when it fits beside one block's columns
+    // and workspace (the one-shot path's peak), else in host memory
+    const size_t d = (size_t)fin->d, d16 = d * sizeof(double2);
+    X->budget = device_budget(o);
+    size_t block_peak = 0;
+    for (auto& B : X->blocks)
+        block_peak = std::max(block_peak, (size_t)n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2) +
+                                              krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), false));
+    const int Mf = std::min(o->M, (int)d);
+    const bool fin_planes_dev = (size_t)n_t * d16 + krylov_bytes({fin}, Mf, true) <= X->budget;
+    if ((size_t)n_t * d16 + block_peak <= X->budget &&
+        (size_t)n_t * d16 + krylov_bytes({fin}, Mf, false) <= X->budget) {
+        if (cudaMalloc(&X->phi, sizeof(double2) * n_t * d) != cudaSuccess) {
+            cudaGetLastError();
+            X->phi = nullptr;
+        }
+    }
+    if (!X->phi) {
+        if (cudaMalloc(&X->phi_stage, d16) != cudaSuccess) {
+            set_error("cannot hold one Phi(t_k) of dimension %zu", d);
+            return fail(KG_ENOMEM);
+        }
+        if (cudaHostAlloc(&X->phi_host, sizeof(double2) * n_t * d, cudaHostAllocDefault) == cudaSuccess) {
+            X->phi_pinned = true;
+        } else {
+            cudaGetLastError();
+            X->phi_host = static_cast<double2*>(std::malloc(sizeof(double2) * n_t * d));
+            if (!X->phi_host) {
+                set_error("cannot hold Phi(t_k) for %d times in device or host memory", n_t);
+                return fail(KG_ENOMEM);
+            }
+        }
+    }
+    // step (ii): Phi(t_k) = e^{-iH t_k} |0>, stored on the grid
+    auto put = [&](int k, const double2* src) -> int {
+        const cudaError_t e =
+            X->phi ? cudaMemcpyAsync(X->phi + k * d, src, d16, cudaMemcpyDeviceToDevice, st)
+                   : cudaMemcpyAsync(X->phi_host + k * d, src, d16, cudaMemcpyDeviceToHost, st);
+        return e == cudaSuccess ? KG_OK : cuda_fail(e, "Phi(t_k) store", __FILE__, __LINE__);
+    };
+    int rc = put(0, ini->gs);
+    if (rc == KG_OK && n_t > 1) {
+        Krylov K;
+        StepRunner R;
+        rc = krylov_alloc(K, {fin}, Mf, fin->nsm, o->schedule, X->phi ? fin_planes_dev : true);
+        if (rc == KG_OK) {
+            K.hdesc[0].tau = dt / X->n_sub;
+            rc = krylov_upload(K, st);
+        }
+        if (rc == KG_OK)
+            rc = cudaMemcpyAsync(K.vec(0, 0), ini->gs, d16, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK
+                                                                                                         : KG_ECUDA;
+        if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
+        for (int k = 1; rc == KG_OK && k < n_t; ++k) {
+            for (int n = 0; rc == KG_OK && n < X->n_sub; ++n) rc = R.run(st);
+            if (rc == KG_OK) rc = put(k, K.vec(0, 0));
+        }
+        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        R.release();
+        krylov_free(K);
+    } else if (rc == KG_OK) {
+        rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+    }
+    if (rc != KG_OK) return fail(rc);
+    plan_blocks(X);
     *out = X;
     return KG_OK;
 }
@@ -917,6 +1045,11 @@ void keldysh_free(kg_keldysh* X) {
     if (!X) return;
     for (auto& B : X->blocks) block_release(B);
     cudaFree(X->phi);
+    cudaFree(X->phi_stage);
+    if (X->phi_pinned)
+        cudaFreeHost(X->phi_host);
+    else
+        std::free(X->phi_host);
     delete X;
 }
 
@@ -930,15 +1063,21 @@ int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk) {
     if (G_les_kk) std::memset(G_les_kk, 0, sizeof(double) * 2 * n * n);
     if (G_gtr_kk) std::memset(G_gtr_kk, 0, sizeof(double) * 2 * n * n);
     for (auto& B : X->blocks) {
-        KG_TRY(block_prepare(X, B, st));
-        KG_TRY(block_row(X, B, k, st));
+        int rc = block_prepare(X, B, st, X->keep_stores ? X->n_t : 1, X->planes);
+        if (rc == KG_OK) rc = block_row(X, B, k, st);
         const int na = (int)B.idx.size(), dn = (int)B.nb->d;
-        const double2* xs = B.store + (size_t)k * na * dn;
-        KG_TRY(launch_inner_lib(xs, na, xs, na, dn, B.ovbuf, na, st));
+        const double2* xs = B.store + (B.slots > 1 ? (size_t)k * na * dn : 0);
+        if (rc == KG_OK) rc = launch_inner_lib(xs, na, xs, na, dn, B.ovbuf, na, st);
         std::vector<double2> h((size_t)na * na);
-        KG_CUDA(cudaMemcpyAsync(h.data(), B.ovbuf, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
-        KG_CUDA(cudaStreamSynchronize(st));
-        KG_TRY(block_status(B));
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(h.data(), B.ovbuf, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "row readback", __FILE__, __LINE__);
+        if (rc == KG_OK) rc = block_status(B);
+        if (!X->keep_krylov) block_release_krylov(B);
+        if (!X->keep_stores) block_release(B);
+        if (rc != KG_OK) return rc;
         double* G = B.dagger ? G_gtr_kk : G_les_kk;
         if (!G) continue;
         for (int bb = 0; bb < na; ++bb)
@@ -966,6 +1105,11 @@ int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk) {
 }
 
 int keldysh_gram(kg_keldysh* X, double* G_les, double* G_gtr) {
+    if (!X->keep_stores) {
+        set_error("the memory plan keeps no columns for step (iv) (they exceed the budget); "
+                  "kg_green_keldysh computes the grid one block at a time");
+        return KG_EINVAL;
+    }
     for (int k = 0; k < X->n_t; ++k)
         if (!X->row_done[k]) {
             set_error("row %d of step (iii) not computed", k);
@@ -991,16 +1135,32 @@ int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in) {
         set_error("row %d outside [0, %d)", k, X->n_t);
         return KG_EINVAL;
     }
-    cudaStream_t st = pick_stream(X->fin, &X->o);
     const size_t d = (size_t)X->fin->d;
+    if (!X->phi) {  // host placement
+        if (phi_host) std::memcpy(phi_host, X->phi_host + k * d, sizeof(double2) * d);
+        if (phi_in) {
+            std::memcpy(X->phi_host + k * d, phi_in, sizeof(double2) * d);
+            if (X->staged == k) X->staged = -1;
+        }
+        return KG_OK;
+    }
+    cudaStream_t st = pick_stream(X->fin, &X->o);
     if (phi_host) KG_CUDA(cudaMemcpyAsync(phi_host, X->phi + k * d, sizeof(double2) * d, cudaMemcpyDeviceToHost, st));
     if (phi_in) KG_CUDA(cudaMemcpyAsync(X->phi + k * d, phi_in, sizeof(double2) * d, cudaMemcpyHostToDevice, st));
     KG_CUDA(cudaStreamSynchronize(st));
     return KG_OK;
 }
 
+int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* planes, long long* budget) {
+    if (phi_on_host) *phi_on_host = X->phi ? 0 : (X->phi_pinned ? 1 : 2);
+    if (stores_kept) *stores_kept = X->keep_stores ? 1 : 0;
+    if (planes) *planes = X->planes ? 1 : 0;
+    if (budget) *budget = (long long)X->budget;
+    return KG_OK;
+}
+
 // Whole Keldysh calculation, one (spin, kind) block at a time so that only
-// one block's stored columns are resident.
+// one block's stored columns and workspace are resident.
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                   const kg_opts* o, double* G_les, double* G_gtr) {
     if (!G_les || !G_gtr) {
@@ -1013,12 +1173,18 @@ int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, dou
     const size_t tot = (size_t)n_t * n_t * n_orb * n_orb * 2;
     std::memset(G_les, 0, sizeof(double) * tot);
     std::memset(G_gtr, 0, sizeof(double) * tot);
+    const size_t phi_dev = X->phi ? (size_t)n_t * fin->d * sizeof(double2) : (size_t)fin->d * sizeof(double2);
     int rc = KG_OK;
     for (auto& B : X->blocks) {
-        rc = block_prepare(X, B, st);
+        const size_t store = (size_t)n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2);
+        const bool planes =
+            phi_dev + store + krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), true) <= X->budget;
+        rc = block_prepare(X, B, st, n_t, planes);
         for (int k = 0; rc == KG_OK && k < n_t; ++k) rc = block_row(X, B, k, st);
         if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
         if (rc == KG_OK) rc = block_status(B);
+        // the workspace goes before the Gram, which needs its own scratch
+        block_release_krylov(B);
         std::vector<std::complex<double>> Gm;
         if (rc == KG_OK) rc = gram(B.store, n_t * (int)B.idx.size(), (int)B.nb->d, fin->nsm, Gm, st);
         if (rc == KG_OK) block_assemble(X, B, Gm, B.dagger ? G_gtr : G_les);

@@ -196,7 +196,11 @@ struct Krylov {
 // kg_opts.schedule bits (bit 0: FP64 hop sums instead of the exact integer
 // sums for sectors with uniform hopping; bit 1: step exponential through the
 // eigen-decomposition of T instead of the Taylor series).
-int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule);
+// planes = false leaves out the optional Gram-Schmidt planes (S, V32).
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule,
+                 bool planes = true);
+// Device bytes krylov_alloc takes for these columns (an upper estimate).
+size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes);
 int krylov_upload(Krylov& K, cudaStream_t st);  // after editing hdesc (tau, out, overlaps)
 void krylov_free(Krylov& K);
 int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n, int group = -1);
@@ -289,6 +293,7 @@ void keldysh_free(kg_keldysh* X);
 int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk);
 int keldysh_gram(kg_keldysh* X, double* G_les, double* G_gtr);
 int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in);
+int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                   const kg_opts* o, double* G_les, double* G_gtr);
 int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o);

@@ -25,7 +25,20 @@
 namespace kg {
 
 // ------------------------------------------------------------ workspace
-int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule) {
+size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes) {
+    size_t nv = 0, nw = 0;
+    for (auto* s : cols) {
+        nv += (size_t)(M + 1) * (size_t)s->d;
+        nw += (size_t)s->d;
+    }
+    // basis, W and U, fixed-point image; partial sums (at most 16 blocks per
+    // SM of 72 doubles per column), work lists and descriptors
+    size_t b = nv * sizeof(double2) + 3 * nw * sizeof(double2) + (cols.size() + 2) * (size_t(2) << 20);
+    if (planes) b += nv * (sizeof(double) + sizeof(float2));
+    return b;
+}
+
+int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule, bool planes) {
     K = Krylov();
     K.schedule = schedule;
     const bool int_hops = !(schedule & 1);
@@ -108,7 +121,7 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
     // Planes read by the Gram-Schmidt kernels (Re+Im for the three-multiply
     // dot products, a truncated FP32 copy for the small correction terms).
     // They are optional: without the memory the kernels use V alone.
-    if (cudaMalloc(&K.Sbuf, sizeof(double) * nv) != cudaSuccess ||
+    if (!planes || cudaMalloc(&K.Sbuf, sizeof(double) * nv) != cudaSuccess ||
         cudaMalloc(&K.V32buf, sizeof(float2) * nv) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(K.Sbuf);

@@ -54,7 +54,7 @@ def test_binding_declares_every_signature(kg):
 
 def test_options_and_status_strings(kg):
     o = kg.kg_opts_default()
-    assert (o.M, o.M_gs, o.reorth, o.use_graphs, o.seed) == (20, 100, 1, 1, 1234)
+    assert (o.M, o.M_gs, o.reorth, o.use_graphs, o.seed, o.mem_budget_mb) == (20, 100, 1, 1, 1234, 0)
     assert o.tol_resid == 1e-12 and o.stream is None
     for code in range(0, -9, -1):
         assert kg.kg_strerror(code) != "unknown status"
@@ -153,6 +153,7 @@ def test_every_handle_entry_rejects_null(kg):
     assert lib.kg_green_keldysh(None, None, orb.ctypes.data, 1, 0.1, 1, ob, b, b) == E
     assert lib.kg_keldysh_create(None, None, orb.ctypes.data, 1, 0.1, 1, ob, None) == E
     assert lib.kg_keldysh_gram(None, b, b) == E
+    assert lib.kg_keldysh_plan(None, None, None, None, None) == E
     assert lib.kg_keldysh_get_phi(None, 0, b) == E
     assert lib.kg_keldysh_set_phi(None, 0, b) == E
     assert lib.kg_overlaps(None, 1, b, 1, 4, b, None) == E

@@ -412,6 +412,49 @@ def test_keldysh_internal_substeps_and_phi_roundtrip():
     K.close()
 
 
+@pytest.mark.parametrize("budget_mb,expect", [(0, (0, 1, 1)), (300, (0, 1, 1)), (120, (0, 1, 0)),
+                                               (60, (None, 0, 0))])
+def test_keldysh_memory_plans(budget_mb, expect):
+    """The Keldysh memory plan under device budgets from ample to tight
+    (chain of 10 sites, (5,5), d = 63,504; four blocks of two columns, 8
+    times): everything resident; columns kept with workspaces re-made per
+    row; columns kept without the Gram-Schmidt planes; Phi(t_k) in host
+    memory with rows that keep no columns.  Every plan gives the oracle's
+    grid through kg_green_keldysh, and its rows (and Gram, when the columns
+    are kept) through the staged API."""
+    ini = W.siam_chain(10, 2.0, 5, 5, field=0.4)
+    fin = W.siam_chain(10, 2.0, 5, 5, field=0.0)
+    orbs = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    dt, nt = 0.1, 8
+    rl, rg, _ = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    si, sf = kg.Sector(ini), kg.Sector(fin)
+    opts = kg.kg_opts_default(mem_budget_mb=budget_mb)
+    K = kg.Keldysh(si, sf, orbs, dt, nt, opts)
+    plan = K.plan()
+    got = (plan["phi_on_host"], plan["stores_kept"], plan["planes"])
+    if expect[0] is None:
+        assert got[0] in (1, 2) and got[1:] == expect[1:], plan
+    else:
+        assert got == expect, plan
+    for k in range(nt):
+        dl, dg = K.row(k)
+        assert np.max(np.abs(dl - rl[k, k])) < G_TOL and np.max(np.abs(dg - rg[k, k])) < G_TOL, k
+    if plan["stores_kept"]:
+        Sl, Sg = K.gram()
+        assert np.max(np.abs(Sl - rl)) < G_TOL and np.max(np.abs(Sg - rg)) < G_TOL
+    else:
+        with pytest.raises(kg.KGError) as e:
+            K.gram()
+        assert e.value.code == kg.KG_EINVAL
+    # Phi round trip through the plan's storage
+    phi = K.get_phi(5)
+    K.set_phi(5, phi)
+    assert np.array_equal(K.get_phi(5), phi)
+    K.close()
+    Gl, Gg = kg.kg_green_keldysh(si.handle, sf.handle, orbs, dt, nt, opts)
+    assert np.max(np.abs(Gl - rl)) < G_TOL and np.max(np.abs(Gg - rg)) < G_TOL
+
+
 def test_keldysh_mismatched_sectors():
     a = kg.Sector(W.hubbard_ring(4, 1.0, 2, 2))
     b = kg.Sector(W.hubbard_ring(4, 1.0, 2, 1))
