@@ -681,3 +681,42 @@ def keldysh_entries(ini, fin, samples, dt, gs=None, K=80, tol=1e-12):
                 pair.append(1j * np.vdot(vb, va) if not dagger else -1j * np.vdot(va, vb))
         out.append(tuple(pair))
     return out
+
+
+def green_equilibrium_dense(model, orbitals, dt, n_steps):
+    """The equilibrium G^>(t_k), G^<(t_k) of green_equilibrium by the Lehmann
+    sum (Section 3, Eq. (psigreen) with eta = 0 and the hole part after Eq.
+    (gomega)) from the dense eigen-decompositions of the sector and its
+    neighbours (small sectors only):
+
+      G^>_{aa'}(t) = -i sum_m <0|c_a|m><m|c^dag_a'|0> e^{-i(E_m - E0) t},
+      G^<_{aa'}(t) = +i sum_m <0|c^dag_a'|m><m|c_a|0> e^{+i(E_m - E0) t},
+
+    |m>, E_m the eigenpairs of the N+1 (N-1) sector.  Returns (G_gtr, G_les,
+    E0, gap) with gap = E_1 - E0 of the sector (the degeneracy test)."""
+    sec = Sector(model)
+    w0, Q0 = _eigh(dense_hamiltonian(sec))
+    E0, psi = w0[0], Q0[:, 0]
+    gap = w0[1] - w0[0] if w0.size > 1 else np.inf
+    n = len(orbitals)
+    t = dt * np.arange(n_steps + 1)
+    G_gtr = np.zeros((n_steps + 1, n, n), dtype=np.complex128)
+    G_les = np.zeros_like(G_gtr)
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger, G in ((True, G_gtr), (False, G_les)):
+            nb = sec.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            E, Q = _eigh(dense_hamiltonian(nb))
+            u = np.stack([sec.apply_cop(nb, orbitals[a][0], spin, dagger, psi) for a in idx])
+            p = u @ Q.conj()                                   # p[a, m] = <m|u_a>
+            if dagger:
+                ph = np.exp(-1j * np.outer(t, E - E0))         # [t, m]
+                blk = -1j * np.einsum("am,bm,tm->tab", p.conj(), p, ph)
+            else:
+                ph = np.exp(1j * np.outer(t, E - E0))
+                blk = 1j * np.einsum("bm,am,tm->tab", p.conj(), p, ph)
+            G[np.ix_(range(n_steps + 1), idx, idx)] = blk
+    return G_gtr, G_les, E0, gap

@@ -798,3 +798,20 @@ def test_keldysh_entries_share_work_and_match_single_entries():
         rl, rg = oracle.keldysh_entry(ini, fin, a, b, dt, k, l)
         assert abs(les - rl) < 1e-13 and abs(gtr - rg) < 1e-13, (k, l, a, b)
     assert got[3] == (0j, 0j)
+
+
+@pytest.mark.parametrize("seed,L,nu,nd", [(81, 5, 2, 3), (82, 6, 3, 1), (83, 4, 4, 2)])
+def test_dense_lehmann_route_equals_chebyshev_route(seed, L, nu, nd):
+    """The dense Lehmann route (used for many small instances at once) equals
+    the Chebyshev route (pinned above to Jordan-Wigner expm, closed forms and
+    the Hubbard atom) for complex hopping, both spins, a full band (no
+    particle part) and off-diagonal orbital pairs."""
+    m = W.random_model(L, nu, nd, seed=seed, complex_hopping=True)
+    orbs = [(0, 0), (L - 1, 0), (1, 1), (2, 1)]
+    dt, n = 0.1, 30
+    Gg, Gl, E0, gap = oracle.green_equilibrium_dense(m, orbs, dt, n)
+    rg, rl, e_or = oracle.green_equilibrium(m, orbs, dt, n, K=max(80, 200), tol=1e-14)
+    assert gap > 1e-6 and abs(E0 - e_or) < 1e-12 * max(1.0, abs(e_or))
+    assert np.max(np.abs(Gg - rg)) < 1e-11 and np.max(np.abs(Gl - rl)) < 1e-11
+    if nu == L:
+        assert np.all(Gg[:, :2, :2] == 0)
