@@ -187,12 +187,13 @@ def test_propagate_parity(reorth, dt, n):
     assert abs(np.linalg.norm(y) - 1) < 1e-12
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
+@pytest.mark.parametrize("schedule", list(range(8)))
 def test_hop_sum_schedules(schedule):
     """Exact integer hop sums (schedule bit 0 clear) and FP64 hop sums (bit 0
     set), with the step exponential by Taylor series (bit 1 clear) or by the
-    eigen-decomposition of T (bit 1 set), on uniform-hopping models, through
-    propagation and the ground state."""
+    eigen-decomposition of T (bit 1 set), with exact integer Gram-Schmidt
+    dots (bit 2 clear) or FP64 ones (bit 2 set), on uniform-hopping models,
+    through propagation and the ground state."""
     for model in (W.hubbard_ring(10, 4.0, 5, 4), W.siam_chain(9, 3.0, 4, 5, field=0.7)):
         s = kg.Sector(model)
         o = oracle.Sector(model)
@@ -204,6 +205,27 @@ def test_hop_sum_schedules(schedule):
         E0, _, _ = s.ground_state(opts)
         e_or, _, _ = o.ground_state()
         assert abs(E0 - e_or) <= E_TOL * max(1.0, abs(e_or))
+
+
+@pytest.mark.parametrize("reorth", [1, 2])
+def test_exact_dots_equal_fp64_dots(reorth):
+    """The exact integer Gram-Schmidt dots and the FP64 ones give the same
+    propagation to rounding, for complex hopping and a vector whose components
+    span 30 decades (the fixed-point images keep 52 bits of each vector's
+    largest component), and both match the oracle."""
+    m = W.random_model(8, 4, 3, seed=29, complex_hopping=True)
+    s = kg.Sector(m)
+    rng = np.random.default_rng(31)
+    x = W.random_state(s.dim, 14) * 10.0 ** rng.uniform(-30, 0, s.dim)
+    x /= np.linalg.norm(x)
+    out = []
+    for schedule in (0, 4):
+        xd = dev(x)
+        s.propagate(xd, 0.05, 12, kg.kg_opts_default(schedule=schedule, reorth=reorth))
+        out.append(host(xd))
+    assert np.max(np.abs(out[0] - out[1])) < 1e-13
+    ref = oracle.Sector(m).propagate(x, 0.6)
+    assert np.max(np.abs(out[0] - ref)) < 1e-11
 
 
 def test_integer_hop_sums_wide_dynamic_range():
@@ -258,7 +280,7 @@ def test_step_exponential_taylor_vs_eigen(M):
 def test_bad_schedule_rejected():
     s = kg.Sector(W.random_model(4, 2, 2, seed=1))
     with pytest.raises(kg.KGError):
-        s.green_equilibrium([(0, 0)], 0.1, 2, kg.kg_opts_default(schedule=4))
+        s.green_equilibrium([(0, 0)], 0.1, 2, kg.kg_opts_default(schedule=8))
 
 
 # ------------------------------------------------------- equilibrium G
@@ -337,26 +359,58 @@ def test_batched_equilibrium_parity():
     assert np.all(Gg[6, :, 0, 0] == 0)  # full up band: no particle part
 
 
-def test_batched_c4_subset():
+def _c4_dims(m):
+    L, nu, nd = m["L"], m["n_up"], m["n_dn"]
+    dims = [math.comb(L, nu) * math.comb(L, nd)]
+    if nu < L:
+        dims.append(math.comb(L, nu + 1) * math.comb(L, nd))
+    if nu > 0:
+        dims.append(math.comb(L, nu - 1) * math.comb(L, nd))
+    return dims
+
+
+def test_batched_c4_full_size():
+    """The whole batched workload: 256 star instances (L 6..12, random
+    fillings, d from 36 to 853,776) for all 400 steps (dt = 0.05, M = 20) in
+    one batched call.  The 148 instances whose sector and neighbours have at
+    most 5,000 states are compared with the oracle's dense Lehmann route (on
+    the host cores while the GPU works); the larger ones with the
+    per-instance GPU path (the 12 largest and every 8th of the rest).  An
+    instance the batch reports degenerate must be degenerate for the oracle."""
+    from concurrent.futures import ThreadPoolExecutor
     cfg = W.config_c4()
-    models = cfg["models"][:24]
-    secs = [kg.Sector(m) for m in models]
-    Gg, Gl, status = kg.kg_green_equilibrium_batched([s.handle for s in secs], cfg["orbitals"], cfg["dt"], 20,
-                                                     kg.kg_opts_default(M=cfg["M"]))
+    models, orbs, dt, n = cfg["models"], cfg["orbitals"], cfg["dt"], cfg["n_steps"]
+    small = [i for i, m in enumerate(models) if max(_c4_dims(m)) <= 5000]
+    assert len(small) == 148
+
+    def oracle_side():
+        return {i: oracle.green_equilibrium_dense(models[i], orbs, dt, n) for i in small}
+
+    with ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle_side)
+        secs = [kg.Sector(m) for m in models]
+        opts = kg.kg_opts_default(M=cfg["M"])
+        Gg, Gl, status = kg.kg_green_equilibrium_batched([s.handle for s in secs], orbs, dt, n, opts)
+        assert set(np.unique(status)) <= {kg.KG_OK, kg.KG_EDEGEN}, np.unique(status)
+        large = sorted((i for i in range(len(models)) if i not in small), key=lambda i: -_c4_dims(models[i])[0])
+        plain = large[:12] + large[12::8]
+        for i in plain:
+            if status[i] != kg.KG_OK:
+                continue
+            pg, pl = kg.Sector(models[i]).green_equilibrium(orbs, dt, n, opts)
+            assert np.max(np.abs(Gg[i] - pg)) < 1e-12 and np.max(np.abs(Gl[i] - pl)) < 1e-12, i
+        ref = fut.result()
     checked = 0
-    for i, m in enumerate(models):
-        if status[i] != 0:
-            assert status[i] in (kg.KG_EDEGEN,), status[i]
+    for i in small:
+        rg, rl, E0, gap = ref[i]
+        if status[i] == kg.KG_EDEGEN:
+            assert gap < 1e-6 * max(1.0, abs(E0)), (i, gap)
             continue
-        if math.comb(m["L"], m["n_up"]) * math.comb(m["L"], m["n_dn"]) > 60000:
-            continue  # oracle time; the larger ones are covered by the plain-path comparison below
-        rg, rl, _ = oracle.green_equilibrium(m, cfg["orbitals"], cfg["dt"], 20)
+        if gap < 1e-8 * max(1.0, abs(E0)):
+            continue  # degenerate for the oracle: G is not unique
         assert np.max(np.abs(Gg[i] - rg)) < G_TOL and np.max(np.abs(Gl[i] - rl)) < G_TOL, i
         checked += 1
-    assert checked >= 12
-    big = int(np.argmax([math.comb(m["L"], m["n_up"]) * math.comb(m["L"], m["n_dn"]) for m in models]))
-    pg, pl = kg.Sector(models[big]).green_equilibrium(cfg["orbitals"], cfg["dt"], 20, kg.kg_opts_default(M=cfg["M"]))
-    assert np.max(np.abs(Gg[big] - pg)) < 1e-12 and np.max(np.abs(Gl[big] - pl)) < 1e-12
+    assert checked >= 140
 
 
 # ------------------------------------------------------------- Keldysh G
