@@ -211,7 +211,7 @@ def run_ours(args):
     phi_host = torch.empty(sf.dim, dtype=torch.complex128).pin_memory()
     phi_host.numpy()[:] = K.get_phi(k_row)
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ke = max(1, min(args.steps, 3))
+    ke = args.steps
     torch.cuda.synchronize()
     e2.record(stream)
     for _ in range(ke):
@@ -285,10 +285,22 @@ def run_ours(args):
                 nb_sec.hpsi(xs[i], ys[i], stream)
         h1.record(stream)
         torch.cuda.synchronize()
-    t_h = h0.elapsed_time(h1) * 1e-3 / (reps * nbuf)
+        # device time of each call (its kernels between CUDA events on the
+        # launch stream), without the host's issue gaps between calls
+        kg.kg_profile_start()
+        for _ in range(reps):
+            for i in range(nbuf):
+                nb_sec.hpsi(xs[i], ys[i], stream)
+        hprof = kg.kg_profile_stop()
+    t_wall = h0.elapsed_time(h1) * 1e-3 / (reps * nbuf)
+    n_h, ms_h = hprof.get("hpsi", (1, float("nan")))
+    t_h = ms_h * 1e-3 / max(1, n_h)
     hpsi = {"d": d_nb, "us": round(t_h * 1e6, 2), "gbs": round(32.0 * d_nb / t_h / 1e9, 1),
             "frac_hbm": round(32.0 * d_nb / t_h / 1e9 / peaks["hbm_gbs"], 4),
-            "algorithmic_bytes": 32 * d_nb, "l2": "12 rotating x/y pairs, 281 MB > L2"}
+            "us_back_to_back": round(t_wall * 1e6, 2),
+            "algorithmic_bytes": 32 * d_nb, "l2": "12 rotating x/y pairs, 281 MB > L2",
+            "timing": "device time per call from CUDA events around its kernels; us_back_to_back includes "
+                      "the host's issue time between calls"}
 
     # ---- CPU baseline: the oracle on the host cores, a bounded sample
     cpu = None
@@ -296,13 +308,17 @@ def run_ours(args):
         cpu = cpu_baseline_sample(args.cpu_seconds)
 
     # ---- the batched and adjoint forms against the plain GPU path
-    batched = adjoint = spectral = None
+    batched = adjoint = spectral = c2_full = c3_row = None
     if rank == 0 and world == 1 and not args.no_extras:
-        batched = batched_vs_plain(args.batch_instances, args.batch_steps)
+        batched = batched_vs_plain(args.batch_instances, args.batch_steps, args.plain_steps)
         adjoint = adjoint_vs_fd()
         spectral = lanczos_spectral(si, opts)
         spectral["fine_grid"] = fine_grid_vs_plain(si, opts)
         spectral["fourier"] = fourier_transform(fp64)
+        if not args.no_c2_full:
+            c2_full = c2_full_grid(si, sf, opts)
+    if rank == 0 and world == 1 and args.c3:
+        c3_row = c3_rows(args.c3_nt)
 
     if rank == 0:
         clocks = clk.summary()
@@ -318,7 +334,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernels": kernels, "hpsi": hpsi,
             "fp64_tflops_measured": round(fp64, 3), "cpu_baseline": cpu, "clocks": clocks,
             "setup_s": round(t_setup, 2), "E0_ini": E0, "gs_resid": res,
-            "batched": batched, "adjoint": adjoint, "spectral": spectral,
+            "batched": batched, "adjoint": adjoint, "spectral": spectral, "c2_full": c2_full, "c3_row": c3_row,
         }
         print(json.dumps(line))
     if world > 1:
@@ -331,11 +347,72 @@ def row_workload(k_row):
             "%d G-steps (dt=0.05, M=20, full reorth) + G(t_k,t_k) block" % (k_row, k_row))
 
 
-def batched_vs_plain(n_inst, n_steps):
+def c2_full_grid(si, sf, opts):
+    """Time to solution of the whole c2 quench through the C ABI's one-shot
+    call kg_green_keldysh: step (ii) (Phi on 100 times), step (iii) for every
+    row (both kinds, 12 columns each, k backward G-steps in row k) and the
+    step-(iv) Gram of 1,200 vectors per kind, results on the host.  The ground
+    state of H_ini is the benchmark's own (already computed)."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c2()
+    orbs, dt, n_t = cfg["orbitals"], cfg["dt"], cfg["n_t"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gl, Gg = kg.kg_green_keldysh(si.handle, sf.handle, orbs, dt, n_t, opts)
+    sec = time.perf_counter() - t0
+    gsteps = (n_t - 1) + 2 * len(orbs) * n_t * (n_t - 1) // 2
+    t = np.arange(n_t)
+    sum_rule = float(np.max(np.abs(1j * (Gg[t, t] - Gl[t, t]) - np.eye(len(orbs))[None])))
+    transl = float(max(np.max(np.abs(np.roll(np.roll(G, 1, 2), 1, 3) - G)) for G in (Gl, Gg)))
+    return {"workload": "c2 quench, whole 100x100 grid, all 12x12 spin-up pairs, G^< and G^> (Phi steps, every row of "
+                        "step (iii), 1200-vector Gram per kind) through kg_green_keldysh",
+            "seconds": round(sec, 2), "gsteps": gsteps, "gsteps_per_s": round(gsteps / sec, 1),
+            "max_sum_rule_dev": sum_rule, "max_translation_dev": transl}
+
+
+def c3_rows(n_t):
+    """Rows of the 16-site-chain quench at full size (d = 130,873,600;
+    columns of 91.6M and 147.2M states): ground state of H_ini, Phi on n_t
+    grid times (t_k = 0.2 k, internal step 0.05), then the last row's step
+    (iii) for the impurity's four blocks, timed."""
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c3()
+    t0 = time.perf_counter()
+    si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+    opts = kg.kg_opts_default(M=cfg["M"], dt_internal=cfg["dt_internal"], M_gs=40, tol_resid=1e-10,
+                              max_restarts=400)
+    E0, res, _ = si.ground_state(opts)
+    K = kg.Keldysh(si, sf, cfg["orbitals"], cfg["dt"], n_t, opts)
+    setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    k = n_t - 1
+    t1 = time.perf_counter()
+    dl, dg = K.row(k)
+    sec = time.perf_counter() - t1
+    n_sub = int(round(cfg["dt"] / cfg["dt_internal"]))
+    gsteps = 4 * k * n_sub
+    plan = K.plan()
+    K.close()
+    return {"workload": "c3 16-site chain (7,7) d=130873600, row t_%d of step (iii): 4 columns (both spins, c and "
+                        "c^dag; d=91.6M / 147.2M) x %d G-steps (dt_int=0.05, M=20)" % (k, k * n_sub),
+            "setup_s": round(setup, 2), "seconds": round(sec, 2), "gsteps": gsteps,
+            "gsteps_per_s": round(gsteps / sec, 3), "E0": E0, "gs_resid": res, "plan": plan,
+            "sum_rule_dev": float(abs(1j * (dg[0, 0] - dl[0, 0]) - 1.0))}
+
+
+def batched_vs_plain(n_inst, n_steps, plain_steps):
     """Equilibrium G_imp of the first n_inst star instances of the batched
     workload (256 instances, L in [6, 12], random fillings; dt = 0.05, M = 20,
-    orbital (0, up)), once through kg_green_equilibrium_batched and once
-    instance by instance through kg_green_equilibrium.  Ground states are
+    orbital (0, up)): n_steps steps through kg_green_equilibrium_batched, and
+    plain_steps steps instance by instance through kg_green_equilibrium (the
+    same steps repeat, so the two G-step rates compare).  Ground states are
     computed beforehand (untimed, the same for both); each path is run once
     untimed first (work lists, graphs, autotuning), then timed."""
     import numpy as np
@@ -361,29 +438,33 @@ def batched_vs_plain(n_inst, n_steps):
         except kg.KGError:
             return False  # full or empty up band: that part of G is zero
 
-    gsteps = sum(sum(1 for dag in (False, True) if has_neighbour(s, dag)) * n_steps for s in ok)
-    kg.kg_green_equilibrium_batched([s.handle for s in ok], orbs, dt, n_steps, opts)
+    cols = sum(sum(1 for dag in (False, True) if has_neighbour(s, dag)) for s in ok)
+    gsteps = cols * n_steps
+    kg.kg_green_equilibrium_batched([s.handle for s in ok], orbs, dt, min(n_steps, 4), opts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Gb, Lb, st = kg.kg_green_equilibrium_batched([s.handle for s in ok], orbs, dt, n_steps, opts)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     for s in ok[:4]:
-        s.green_equilibrium(orbs, dt, n_steps, opts)
+        s.green_equilibrium(orbs, dt, 2, opts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     err = 0.0
     for i, s in enumerate(ok):
-        g, l = s.green_equilibrium(orbs, dt, n_steps, opts)
-        err = max(err, float(np.max(np.abs(g - Gb[i]))), float(np.max(np.abs(l - Lb[i]))))
+        g, l = s.green_equilibrium(orbs, dt, plain_steps, opts)
+        err = max(err, float(np.max(np.abs(g - Gb[i, :plain_steps + 1]))),
+                  float(np.max(np.abs(l - Lb[i, :plain_steps + 1]))))
     torch.cuda.synchronize()
     tp = time.perf_counter() - t0
+    plain_rate = cols * plain_steps / tp
     return {"workload": "first %d of 256 star-SIAM instances (L 6..12, random fillings, seed 20240501), "
-                        "%d steps of dt=0.05, M=20, orbital (0,up), G^> and G^<" % (n_inst, n_steps),
+                        "%d steps of dt=0.05 batched (%d per instance on the plain path), M=20, orbital (0,up), "
+                        "G^> and G^<" % (n_inst, n_steps, plain_steps),
             "instances": len(ok), "gsteps": gsteps, "unit": "G-steps/s",
-            "batched_value": round(gsteps / tb, 1), "plain_value": round(gsteps / tp, 1),
-            "batched_s": round(tb, 3), "plain_s": round(tp, 3), "speedup": round(tp / tb, 2),
-            "max_abs_diff": err}
+            "batched_value": round(gsteps / tb, 1), "plain_value": round(plain_rate, 1),
+            "batched_s": round(tb, 3), "plain_s": round(tp, 3), "plain_steps": plain_steps,
+            "speedup": round(gsteps / tb / plain_rate, 2), "max_abs_diff": err}
 
 
 def lanczos_spectral(si, opts, n=100):
@@ -513,9 +594,24 @@ def cpu_baseline_sample(budget_s):
         el = time.perf_counter() - t0
         if el > budget_s or n >= 200:
             break
-    return {"value": round(n / el, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same oracle on one core, a shorter sample
+    oracle.set_num_threads(1)
+    try:
+        n1, t1 = 0, time.perf_counter()
+        while True:
+            x = sec.propagate(x, -cfg["dt"])
+            n1 += 1
+            el1 = time.perf_counter() - t1
+            if el1 > budget_s / 2 or n1 >= 50:
+                break
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": round(n / el, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d oracle G-steps (Chebyshev exp(+iH*0.05) of one c2 N-1 column, d=%d) in %.1f s"
-                      % (n, sec.dim, el)}
+                      % (n, sec.dim, el),
+            "single_thread": {"value": round(n1 / el1, 4), "unit": UNIT, "cores": 1,
+                              "sample": "%d oracle G-steps of the same column on one thread in %.1f s" % (n1, el1)}}
 
 
 def run_reference(args):
@@ -562,7 +658,21 @@ def run_ncu_case(args):
     import paper_1109_1205_gb300 as kg
     import workloads as W
     cfg = W.config_c2()
-    opts = kg.kg_opts_default(M=cfg["M"], reorth=1)
+    opts = kg.kg_opts_default(M=cfg["M"], reorth=1, schedule=args.schedule)
+    if args.ncu_hpsi:
+        # the standalone H*psi on a column of the N-1 sector, three calls
+        # inside the NVTX range "hpsi"
+        nb = kg.Sector(W.with_sector(cfg["fin"], 5, 6))
+        x = torch.randn(nb.dim, dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("hpsi")
+        for _ in range(3):
+            nb.hpsi(x, y, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"ncu_case": "standalone H*psi, d=%d" % nb.dim, "launches": kg.kg_launch_count()}))
+        return
     si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
     si.ground_state(opts)
     K = kg.Keldysh(si, sf, cfg["orbitals"][:args.ncu_orbitals], cfg["dt"], 3, opts)
@@ -587,11 +697,17 @@ def main():
     ap.add_argument("--ref-gsteps", type=int, default=4)
     ap.add_argument("--ncu-case", action="store_true", help="small case for full ncu captures")
     ap.add_argument("--ncu-orbitals", type=int, default=6, help="orbitals of the ncu case (12 = the full row)")
+    ap.add_argument("--ncu-hpsi", action="store_true", help="ncu case: the standalone H*psi instead of a row")
+    ap.add_argument("--schedule", type=int, default=0, help="kg_opts.schedule of the ncu case")
     ap.add_argument("--fourier-case", action="store_true",
                     help="only the damped Fourier transform extra (for ncu captures of k_fourier)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint comparisons")
-    ap.add_argument("--batch-instances", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=400)
+    ap.add_argument("--plain-steps", type=int, default=100)
+    ap.add_argument("--no-c2-full", action="store_true", help="skip the whole-grid c2 time to solution")
+    ap.add_argument("--c3", action="store_true", help="also time a row of the 16-site chain at full size")
+    ap.add_argument("--c3-nt", type=int, default=3, help="grid times of the c3 row extra (row n_t - 1 is timed)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)

@@ -78,7 +78,10 @@ typedef struct kg_opts {
                            exponential e^{-iT tau} e_1 through the eigen-
                            decomposition of T (Section 3, Eq. (udelta)),
                            instead of the scaled Taylor series of the same
-                           vector (0)                                           */
+                           vector; bit 2: Gram-Schmidt dot products in FP64
+                           (three multiply-adds per complex product) instead
+                           of exact integer products of 52-bit fixed-point
+                           images of the Lanczos vectors (0)                     */
     int use_graphs;     /* replay each propagation step as a CUDA graph (1)    */
     double dt_internal; /* Keldysh: Krylov step inside one grid step; 0 = dt   */
     unsigned long long seed; /* ground-state start vector seed (1234)         */
@@ -121,8 +124,9 @@ int kg_sector_strings(const kg_sector* s, unsigned int* up_host, unsigned int* d
  * stream: cudaStream_t; NULL means CUDA's legacy default stream.
  * Asynchronous (stream-ordered).  When all hops of the sector share one
  * amplitude, the hop sums are exact 64-bit integer sums of a fixed-point
- * image of x, held in 16 d bytes of stream-ordered scratch (cudaMallocAsync
- * from the device's default pool, freed on the same stream). */
+ * image of x, held in 16 d bytes of scratch that the sector owns (allocated
+ * by the first such call, freed with the sector): calls with one sector must
+ * therefore be ordered (one stream, or synchronised), as for any handle. */
 int kg_hpsi(kg_sector* s, const double* x_dev, double* y_dev, void* stream);
 
 /* ---- c / c^dag sector maps ------------------------------------------

@@ -221,7 +221,6 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 static int cg_projected(kg_sector* s, const double2* gs, double E0, const double2* z, double2* x, double tol,
                         int maxit, cudaStream_t st) {
     const int d = (int)s->d;
-    const SecView S = s->view();
     double2 *r = nullptr, *p = nullptr, *Ap = nullptr, *sc = nullptr;
     KG_CUDA(cudaMalloc(&r, sizeof(double2) * d));
     KG_CUDA(cudaMalloc(&p, sizeof(double2) * d));
@@ -249,7 +248,7 @@ static int cg_projected(kg_sector* s, const double2* gs, double E0, const double
     if (rc != KG_OK || rz == 0.0) return fin(rc);
     if (cudaMemcpyAsync(p, r, sizeof(double2) * d, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return fin(KG_ECUDA);
     for (int it = 0; rc == KG_OK && it < maxit; ++it) {
-        if ((rc = launch_hpsi(S, p, Ap, st)) != KG_OK) break;
+        if ((rc = launch_hpsi(s, p, Ap, st)) != KG_OK) break;
         if ((rc = axpby(-E0, p, 1.0, Ap, d, st)) != KG_OK) break;
         if ((rc = project(Ap)) != KG_OK) break;
         std::complex<double> pAp;

@@ -14,7 +14,7 @@ int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o
         set_error("NULL vector or negative step count");
         return KG_EINVAL;
     }
-    if (o->M < 1 || o->M > kMaxM || o->reorth < 0 || o->reorth > 2 || o->schedule < 0 || o->schedule > 3) {
+    if (o->M < 1 || o->M > kMaxM || o->reorth < 0 || o->reorth > 2 || o->schedule < 0 || o->schedule > 7) {
         set_error("bad M or reorth");
         return KG_EINVAL;
     }
@@ -116,7 +116,7 @@ int kg_hpsi(kg_sector* s, const double* x_dev, double* y_dev, void* stream) {
         return KG_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;  // NULL: the legacy default stream
-    return launch_hpsi(s->view(), reinterpret_cast<const double2*>(x_dev), reinterpret_cast<double2*>(y_dev), st);
+    return launch_hpsi(s, reinterpret_cast<const double2*>(x_dev), reinterpret_cast<double2*>(y_dev), st);
 }
 
 int kg_neighbour_dim(kg_sector* s, int spin, int dagger, long long* dim) {

@@ -99,8 +99,8 @@ static int check_opts(const kg_opts* o) {
         set_error("reorth must be 0, 1 or 2");
         return KG_EINVAL;
     }
-    if (o->schedule < 0 || o->schedule > 3) {
-        set_error("schedule must be in [0, 3]");
+    if (o->schedule < 0 || o->schedule > 7) {
+        set_error("schedule must be in [0, 7]");
         return KG_EINVAL;
     }
     return KG_OK;

@@ -291,6 +291,7 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
     const bool pre = MODE == 3 && j > 0 && D.Xf != nullptr && Ef >= E && Ef - E <= kFixSlack;
     const double2* x = D.V + (size_t)j * D.d;
     const double2* xp = D.V + (size_t)(j > 0 ? j - 1 : 0) * D.d;
+    const int E0img = C->eimg[0];
     double2* w = D.W;
     double acc[2] = {0.0, 0.0};
     int ew = 0;
@@ -320,6 +321,7 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
             r.y = fma(sdiag, xv.y, fma(sj, hop.y, -cprev * p.y));
         }
         w[idx] = r;
+        if (j == 0 && D.I) D.I[idx] = fix_image(xv, E0img);  // image of V_0 for the exact dots
         acc[0] = fma(xv.x, r.x, fma(xv.y, r.y, acc[0]));  // Re conj(x) r
         ew = max(ew, max(exp_field(r.x), exp_field(r.y)));
     }
@@ -349,33 +351,34 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, 
     lanczos_hpsi_item<MODE>(desc, cs, j, cnt, items[blockIdx.x], sh);
 }
 
-int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st) {
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int nb = std::max(1, std::min((S.d + kThreads - 1) / kThreads, nsm * 8));
+int launch_hpsi(kg_sector* s, const double2* x, double2* y, cudaStream_t st) {
+    const SecView S = s->view();
+    const int nb = std::max(1, std::min((S.d + kThreads - 1) / kThreads, s->nsm * 8));
     if (S.hopmode == 0 && S.fix_pre >= 0) {
-        // largest exponent of x, the fixed-point image of x on it (stream-
-        // ordered scratch, so calls on different streams do not share it),
-        // then exact hop sums that add the image's integers
-        ProfScope ps("hpsi", st);
-        char* scratch = nullptr;
-        const size_t off = 256;  // the exponent, then the image (16-byte aligned)
-        KG_CUDA(cudaMallocAsync((void**)&scratch, off + sizeof(longlong2) * (size_t)S.d, st));
-        int* d_emax = reinterpret_cast<int*>(scratch);
-        longlong2* xf = reinterpret_cast<longlong2*>(scratch + off);
-        int rc = KG_OK;
-        if (cudaMemsetAsync(d_emax, 0, sizeof(int), st) != cudaSuccess) rc = KG_ECUDA;
-        if (rc == KG_OK) {
-            k_maxexp<<<std::min(nb, nsm * 4), kThreads, 0, st>>>(x, S.d, d_emax);
-            k_tofix<<<nb, kThreads, 0, st>>>(x, S.d, d_emax, S.fix_pre, xf);
-            k_hpsi_pre<<<nb, kThreads, 0, st>>>(S, x, xf, y, d_emax);
-            const cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) rc = cuda_fail(e, "kernel launch", __FILE__, __LINE__);
-            else count_launch(3);
+        // largest exponent of x, the fixed-point image of x on it, then exact
+        // hop sums that add the image's integers.  The scratch belongs to the
+        // sector (allocated once, on the first call), so calls with one
+        // sector must be ordered, like every use of a handle.
+        if (!s->hp_xf) {
+            if (cudaMalloc(&s->hp_emax, 256) != cudaSuccess ||
+                cudaMalloc(&s->hp_xf, sizeof(longlong2) * (size_t)S.d) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(s->hp_emax);
+                s->hp_emax = nullptr;
+                s->hp_xf = nullptr;
+                set_error("H*psi scratch of %d elements", S.d);
+                return KG_ENOMEM;
+            }
         }
-        cudaFreeAsync(scratch, st);
-        return rc;
+        ProfScope ps("hpsi", st);
+        KG_CUDA(cudaMemsetAsync(s->hp_emax, 0, sizeof(int), st));
+        k_maxexp<<<std::min(nb, s->nsm * 4), kThreads, 0, st>>>(x, S.d, s->hp_emax);
+        k_tofix<<<nb, kThreads, 0, st>>>(x, S.d, s->hp_emax, S.fix_pre, s->hp_xf);
+        k_hpsi_pre<<<nb, kThreads, 0, st>>>(S, x, s->hp_xf, y, s->hp_emax);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch", __FILE__, __LINE__);
+        count_launch(3);
+        return KG_OK;
     }
     ProfScope ps("hpsi", st);
     if (S.hopmode == 0)

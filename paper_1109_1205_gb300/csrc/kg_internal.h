@@ -113,6 +113,10 @@ struct kg_sector {
     bool has_gs = false;
     double E0 = 0.0, resid = 0.0, gap = 0.0;
     double2* gs = nullptr;  // [d] cached ground state (unit norm)
+    // scratch of the standalone H*psi (exact hop sums): the largest exponent
+    // and the fixed-point image of the input, allocated on first use
+    int* hp_emax = nullptr;
+    longlong2* hp_xf = nullptr;
     kg::SecView view() const;
 };
 
@@ -128,6 +132,7 @@ struct ColScalars {
     double2 h[kMaxMgs + 1];     // Gram-Schmidt coefficients of the current pass
     double2 c[kMaxMgs];         // combination coefficients (already times scale)
     int emax[kMaxMgs + 1];      // largest biased FP64 exponent among the components of V_k
+    int eimg[kMaxMgs + 1];      // exponent bound of the fixed-point image I_k (exact dots)
     double beta0;               // norm of the start vector
     double lam0, lam1, resest;  // ground-state Ritz value, next one, residual estimate
     double rq, rnorm;           // Rayleigh quotient and residual of a Ritz vector
@@ -148,6 +153,8 @@ struct ColDesc {
     double2* V;             // [M+1][d] Lanczos vectors (unnormalised)
     double* S;              // [M+1][d] Re + Im of each component of V_k (or null)
     float2* V32;            // [M+1][d] V_k truncated to FP32 (or null)
+    int4* I;                // [M+1][d] V_k in 52-bit fixed point on eimg[k], split
+                            // into 26-bit halves {x_hi, x_lo, y_hi, y_lo} (or null)
     longlong2* Xf;          // [d] fixed-point image of the next H*psi input (or null)
     double2* W;             // [d] H v workspace
     double2* U;             // [d] W - a_j v_j, left by the Gram-Schmidt dots
@@ -182,6 +189,7 @@ struct Krylov {
     double2* Vbuf = nullptr;
     double* Sbuf = nullptr;         // planes of the Gram-Schmidt kernels (optional)
     float2* V32buf = nullptr;
+    int4* Ibuf = nullptr;           // fixed-point images of the exact Gram-Schmidt dots
     longlong2* Xfbuf = nullptr;     // fixed-point H*psi inputs of exact-integer columns
     double2* Wbuf = nullptr;
     double* partbuf = nullptr;
@@ -200,14 +208,14 @@ struct Krylov {
 int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, int nsm, int schedule,
                  bool planes = true);
 // Device bytes krylov_alloc takes for these columns (an upper estimate).
-size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes);
+size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes, int schedule = 0);
 int krylov_upload(Krylov& K, cudaStream_t st);  // after editing hdesc (tau, out, overlaps)
 void krylov_free(Krylov& K);
 int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n, int group = -1);
 
 // ----------------------------------------------------------- launchers
-// y = H x (plain).
-int launch_hpsi(const SecView& S, const double2* x, double2* y, cudaStream_t st);
+// y = H x (plain); exact-hop-sum sectors use the sector's own scratch.
+int launch_hpsi(kg_sector* s, const double2* x, double2* y, cudaStream_t st);
 // Lanczos H*psi: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
 // partial sums of a_j = <v_j, w> reduced on the device.
 int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st);
@@ -422,6 +430,30 @@ __device__ __forceinline__ long long fix_term(double x, int E, int P, uint32_t n
     long long v = (long long)((m + half) >> r);
     v = e ? v : 0ll;
     return ((uint32_t)(b >> 63) ^ neg) ? -v : v;
+}
+
+// round(x * 2^(1074 - E)) for E at least the exponent field of x, so that
+// |x| < 2^(E - 1022) and |result| < 2^52: a 52-bit fixed-point number whose
+// unit is 2^-52 of the bound.  Zero and subnormal x give 0.  Integer pipe
+// only (round half away from zero on the magnitude).
+__device__ __forceinline__ long long fix52(double x, int E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // x = m 2^(e - 1075)
+    const int r = min(E + 1 - e, 63);                                              // >= 1
+    long long v = (long long)((m + (1ull << (r - 1))) >> r);
+    v = e ? v : 0ll;
+    return (b >> 63) ? -v : v;
+}
+
+// The two 26-bit halves of a 52-bit fixed-point number: v = hi 2^26 + lo,
+// lo in [0, 2^26), |hi| <= 2^26.
+__device__ __forceinline__ int fix_hi(long long v) { return (int)(v >> 26); }
+__device__ __forceinline__ int fix_lo(long long v) { return (int)(v & 0x3ffffffll); }
+
+__device__ __forceinline__ int4 fix_image(double2 u, int E) {
+    const long long x = fix52(u.x, E), y = fix52(u.y, E);
+    return make_int4(fix_hi(x), fix_lo(x), fix_hi(y), fix_lo(y));
 }
 
 // The fixed-point image of V_{j+1} is written by the update with an exponent

@@ -25,7 +25,7 @@
 namespace kg {
 
 // ------------------------------------------------------------ workspace
-size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes) {
+size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool planes, int schedule) {
     size_t nv = 0, nw = 0;
     for (auto* s : cols) {
         nv += (size_t)(M + 1) * (size_t)s->d;
@@ -34,7 +34,7 @@ size_t krylov_bytes(const std::vector<const kg_sector*>& cols, int M, bool plane
     // basis, W and U, fixed-point image; partial sums (at most 16 blocks per
     // SM of 72 doubles per column), work lists and descriptors
     size_t b = nv * sizeof(double2) + 3 * nw * sizeof(double2) + (cols.size() + 2) * (size_t(2) << 20);
-    if (planes) b += nv * (sizeof(double) + sizeof(float2));
+    if (planes) b += nv * (sizeof(double) + sizeof(float2) + ((schedule & 4) ? 0 : sizeof(int4)));
     return b;
 }
 
@@ -129,6 +129,12 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         K.Sbuf = nullptr;
         K.V32buf = nullptr;
     }
+    // fixed-point images for the exact integer Gram-Schmidt dots (schedule
+    // bit 2 clear), optional like the planes
+    if (K.Sbuf && !(schedule & 4) && cudaMalloc(&K.Ibuf, sizeof(int4) * nv) != cudaSuccess) {
+        cudaGetLastError();
+        K.Ibuf = nullptr;
+    }
     KG_TRY(need(cudaMalloc(&K.Wbuf, sizeof(double2) * 2 * nw), "work vector allocation"));
     if (nx) KG_TRY(need(cudaMalloc(&K.Xfbuf, sizeof(longlong2) * nx), "fixed-point image allocation"));
     KG_TRY(need(cudaMalloc(&K.partbuf, sizeof(double) * np), "partial-sum allocation"));
@@ -146,6 +152,7 @@ int krylov_alloc(Krylov& K, const std::vector<const kg_sector*>& cols, int M, in
         D.V = K.Vbuf + ov;
         D.S = K.Sbuf ? K.Sbuf + ov : nullptr;
         D.V32 = K.V32buf ? K.V32buf + ov : nullptr;
+        D.I = K.Ibuf ? K.Ibuf + ov : nullptr;
         if (D.mode == 3) {
             D.Xf = K.Xfbuf + ox;
             ox += (size_t)D.d;
@@ -173,6 +180,7 @@ void krylov_free(Krylov& K) {
     cudaFree(K.Vbuf);
     cudaFree(K.Sbuf);
     cudaFree(K.V32buf);
+    cudaFree(K.Ibuf);
     cudaFree(K.Xfbuf);
     cudaFree(K.Wbuf);
     cudaFree(K.partbuf);
@@ -262,6 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_colnorm(const ColDesc* desc, const
         C->beta[0] = 0.0;
         C->scale[0] = n > 0.0 ? 1.0 / n : 0.0;
         C->emax[0] = (int)red[1];
+        C->eimg[0] = (int)red[1];  // I_0 is written by the first H*psi on this exponent
         C->m_eff = n > 0.0 ? M : 0;
         // the status is sticky over the steps of one call (reset by
         // launch_reset_status), so a non-finite column stays reported
@@ -390,6 +399,182 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
     }
 }
 
+// Exact-product Gram-Schmidt coefficients (first pass): h_k = s_k <V_k, u>
+// with u = W - a_j v_j, from 52-bit fixed-point images.  Each V_k comes as
+// its image I_k (written by the kernel that produced V_k, on the exponent
+// bound eimg[k]); u is formed in FP64 here and converted on a bound E_u of
+// its largest exponent.  With both numbers split into 26-bit halves, every
+// partial product (hi*hi, hi*lo, lo*hi, lo*lo) is an exact 64-bit integer
+// (one wide integer multiply-add).  Per element the cross and low terms are
+// combined exactly and rounded once, to nearest, to units of 2^52 of the
+// full product (the hi*hi unit): an unbiased error of at most half a unit,
+// 2^-53 of the product of the two vectors' largest components, only where
+// the products are that large.  A thread's sums are converted to FP64 once
+// per tile and reduced in a fixed order.  The FP64 pipe of this GPU issues
+// about 2 multiply-adds per clock per SM, the integer pipe far more, so these
+// dots are bounded by the 16 bytes of I_k per element and vector instead of
+// the 3 FP64 multiply-adds per complex product of the Re+Im form.
+//
+// Each block takes its elements in tiles of kIntTile: first every thread
+// forms kIntTile / kThreads elements of u and their images (shared memory),
+// then the G thread groups take the tile's elements for their KH vectors
+// each, two elements per iteration with all their loads issued first.
+//
+// The update writes I_{j+1} on an exponent bounded before V_{j+1} exists.
+// Near a breakdown (||V_{j+1}|| far below ||W||) that bound is loose and the
+// image keeps too few of V_{j+1}'s own bits; a vector whose bound exceeds
+// its true largest exponent by more than kFixSlack bits is therefore
+// converted here from V_k on its exact exponent, the fresh image is stored
+// back (each block its own elements) and its exponent updated at the end.
+constexpr int kIntTile = 1024;
+
+template <int NK>
+struct IntDots {
+    static constexpr int G = NK <= 3 ? 1 : (NK <= 6 ? 2 : (NK <= 12 ? 4 : 8));  // groups splitting k
+    static constexpr int KH = (NK + G - 1) / G;                                  // vectors per group
+    static constexpr int TG = kThreads / G;                                      // threads per group
+};
+
+// Re and Im of conj(v) u in units of 2^52 of the full product, for v and u
+// given as split 52-bit images (v: {x_hi, x_lo, y_hi, y_lo}; u: Re hi/lo,
+// Im hi/lo and -Re hi/lo).
+__device__ __forceinline__ void cdot_fix(const int4 v, const int* uw, long long& re, long long& im) {
+    const int p1 = uw[0], p0 = uw[1], q1 = uw[2], q0 = uw[3], n1 = uw[4], n0 = uw[5];
+    // Re = vx ux + vy uy
+    long long t = ((long long)v.y * p0 + (long long)v.w * q0) >> 26;
+    t += (long long)v.x * p0 + (long long)v.y * p1 + (long long)v.z * q0 + (long long)v.w * q1;
+    re += (long long)v.x * p1 + (long long)v.z * q1 + ((t + (1ll << 25)) >> 26);
+    // Im = vx uy - vy ux
+    long long s = ((long long)v.y * q0 + (long long)v.w * n0) >> 26;
+    s += (long long)v.x * q0 + (long long)v.y * q1 + (long long)v.z * n0 + (long long)v.w * n1;
+    im += (long long)v.x * q1 + (long long)v.z * n1 + ((s + (1ll << 25)) >> 26);
+}
+
+template <int NK>
+__global__ void __launch_bounds__(kThreads, 3) k_reorth_dots_int(const ColDesc* desc, const int4* items,
+                                                                 ColScalars* cs, int j, int k0, int nk,
+                                                                 unsigned* cnt) {
+    constexpr int G = IntDots<NK>::G, KH = IntDots<NK>::KH, TG = IntDots<NK>::TG;
+    constexpr int R = kIntTile / kThreads;         // elements of u per thread and tile
+    __shared__ int up[kIntTile][6];                // image of u: Re hi/lo, Im hi/lo, -Re hi/lo
+    __shared__ double sm[(kThreads / 32) * 2 * KH];
+    __shared__ double bs[2 * NK], red[2 * NK];
+    __shared__ int eu_s;
+    __shared__ int fresh_s[NK], ek_s[NK];
+    KG_ITEM();
+    if (j >= C->m_eff) return;
+    const int d = D.d;
+    const int grp = threadIdx.x / TG, t = threadIdx.x % TG;
+    const int kb = grp * KH, kn = min(KH, NK - kb);
+    int4* Ib = D.I + (size_t)(k0 + kb) * d;
+    const double2* Vk = D.V + (size_t)(k0 + kb) * d;
+    const double2* w = D.W;
+    const double2* vj = D.V + (size_t)j * d;
+    const double aj = C->alpha[j] * C->scale[j];
+    // the last chunk leaves u = W - a_j v_j in U for the update
+    const bool keep = k0 + NK == j + 1;
+    if (threadIdx.x < NK) {
+        ek_s[threadIdx.x] = C->emax[k0 + threadIdx.x];
+        fresh_s[threadIdx.x] = C->eimg[k0 + threadIdx.x] - C->emax[k0 + threadIdx.x] > kFixSlack;
+    }
+    if (threadIdx.x == 0) {
+        // |u_i| <= |W_i| + |a_j| |V_j[i]| < (1 + |a_j| 2^(E_j - E_w)) 2^(E_w - 1022), with a margin
+        const int Ew = C->ew;
+        const double r = (1.0 + fabs(aj) * ldexp(1.0, C->emax[j] - Ew)) * (1.0 + 1.0 / 1024.0);
+        int ex;
+        const double fr = frexp(r, &ex);
+        eu_s = Ew + (fr == 0.5 ? ex - 1 : ex);
+    }
+    __syncthreads();
+    const int Eu = eu_s;
+    double acc[2 * KH];
+#pragma unroll
+    for (int q = 0; q < 2 * KH; ++q) acc[q] = 0.0;
+    auto load = [&](int k, int i) -> int4 {
+        if (fresh_s[kb + k]) {
+            const int4 v = fix_image(Vk[(size_t)k * d + i], ek_s[kb + k]);
+            Ib[(size_t)k * d + i] = v;
+            return v;
+        }
+        return Ib[(size_t)k * d + i];
+    };
+    for (int base = blk * kIntTile; base < d; base += nblk * kIntTile) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = threadIdx.x + r * kThreads, i = base + e;
+            if (i < d) {
+                double2 u = w[i];
+                const double2 p = vj[i];
+                u.x = fma(-aj, p.x, u.x);
+                u.y = fma(-aj, p.y, u.y);
+                if (keep) D.U[i] = u;
+                const long long px = fix52(u.x, Eu), py = fix52(u.y, Eu);
+                up[e][0] = fix_hi(px);
+                up[e][1] = fix_lo(px);
+                up[e][2] = fix_hi(py);
+                up[e][3] = fix_lo(py);
+                up[e][4] = fix_hi(-px);
+                up[e][5] = fix_lo(-px);
+            }
+        }
+        __syncthreads();
+        const int end = min(kIntTile, d - base);
+        long long re[KH], im[KH];
+#pragma unroll
+        for (int k = 0; k < KH; ++k) re[k] = im[k] = 0;
+        // sums stay below 2^62: at most 2^53.1 per element and kIntTile / TG <= 128 elements
+        for (int e = t; e < end; e += 2 * TG) {
+            const int e2 = e + TG;
+            int4 va[KH], vb[KH];
+#pragma unroll
+            for (int k = 0; k < KH; ++k) {
+                if (k < kn) {
+                    va[k] = load(k, base + e);
+                    if (e2 < end) vb[k] = load(k, base + e2);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KH; ++k) {
+                if (k < kn) {
+                    cdot_fix(va[k], up[e], re[k], im[k]);
+                    if (e2 < end) cdot_fix(vb[k], up[e2], re[k], im[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+            acc[2 * k] += (double)re[k];
+            acc[2 * k + 1] += (double)im[k];
+        }
+        __syncthreads();
+    }
+    // block sums: warps reduce, then each group's warps in warp order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 2 * KH; ++q) {
+        const double v = warp_sum(acc[q]);
+        if (lane == 0) sm[warp * 2 * KH + q] = v;
+    }
+    __syncthreads();
+    constexpr int WG = TG / 32;  // warps per group
+    for (int q = threadIdx.x; q < 2 * NK; q += blockDim.x) {
+        const int g = q / (2 * KH), l = q - g * 2 * KH;
+        double sum = 0.0;
+        for (int w2 = 0; w2 < WG; ++w2) sum += sm[(g * WG + w2) * 2 * KH + l];
+        bs[q] = sum;
+    }
+    __syncthreads();
+    if (grid_finish(bs, 2 * NK, D.part, cnt + b, blk, nblk, red)) {
+        for (int k = threadIdx.x; k < NK; k += blockDim.x) {
+            // units: 2^52 of 2^(E_k - 1074) 2^(E_u - 1074), E_k the exponent of V_k's image
+            const int Ei = fresh_s[k] ? C->emax[k0 + k] : C->eimg[k0 + k];
+            const double f = C->scale[k0 + k] * ldexp(1.0, Ei + Eu - 2096);
+            C->h[k0 + k] = make_double2(f * red[2 * k], f * red[2 * k + 1]);
+            C->eimg[k0 + k] = Ei;
+        }
+    }
+}
+
 // The accumulators of k_reorth_dots are compile-time sized and a kernel
 // built for more vectors than a launch needs would still issue the FP64
 // multiply-adds of the unused slots, so every count up to kChunk has its own
@@ -406,8 +591,38 @@ static DotsKernel dots_kernel(int nk) {
     return exact[nk - 1];
 }
 
+using IntDotsKernel = void (*)(const ColDesc*, const int4*, ColScalars*, int, int, int, unsigned*);
+
+template <int... N>
+static constexpr std::array<IntDotsKernel, sizeof...(N)> int_dots_table(std::integer_sequence<int, N...>) {
+    return {{&k_reorth_dots_int<N + 1>...}};
+}
+
+static IntDotsKernel int_dots_kernel(int nk) {
+    static const std::array<IntDotsKernel, kChunk> exact =
+        int_dots_table(std::make_integer_sequence<int, kChunk>{});
+    return exact[nk - 1];
+}
+
+// The exact integer dots serve first passes when every column has its images.
+static bool use_int_dots(const Krylov& K, bool second) {
+    if (second || (K.schedule & 4) || !K.Ibuf) return false;
+    for (auto& D : K.hdesc)
+        if (!D.I) return false;
+    return true;
+}
+
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
     ProfScope ps("reorth_dots", st);
+    if (use_int_dots(K, second)) {
+        const IntDotsKernel ik = int_dots_kernel(nk);
+        const int4* items;
+        int n;
+        KG_TRY(work_list(K, (const void*)ik, -1, &items, &n));
+        ik<<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, k0, nk, K.cnt);
+        KG_LAUNCHED();
+        return KG_OK;
+    }
     const DotsKernel kern = dots_kernel(nk);
     const int4* items;
     int n;
@@ -542,9 +757,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         em = max(em, max(exp_field(u.x), exp_field(u.y)));
         return u;
     };
-    if (D.Xf && (second || level < 2)) {
+    const bool img = D.I != nullptr && level >= 1;  // images for the exact Gram-Schmidt dots
+    if ((D.Xf || img) && (second || level < 2)) {
         // Last pass of an exact-integer column: also write the fixed-point
-        // image of V_{j+1} that the next H*psi reads, on the exponent efix.
+        // image of V_{j+1} that the next H*psi reads, on the exponent efix;
+        // with the exact dots, also its 52-bit image I_{j+1} on the same one.
         // The vector's largest exponent is only known at the end of this
         // kernel, so efix bounds it from the inputs: every component of the
         // result is below
@@ -566,11 +783,25 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         }
         __syncthreads();
         const int Ef = efix_s, P = D.fix_pre;
-        KG_FOR(i) {
-            const double2 u = element(i);
-            D.Xf[i] = make_longlong2(fix_term(u.x, Ef, P, 0u), fix_term(u.y, Ef, P, 0u));
+        int4* I1 = img ? D.I + (size_t)(j + 1) * d : nullptr;
+        if (D.Xf && img) {
+            KG_FOR(i) {
+                const double2 u = element(i);
+                D.Xf[i] = make_longlong2(fix_term(u.x, Ef, P, 0u), fix_term(u.y, Ef, P, 0u));
+                I1[i] = fix_image(u, Ef);
+            }
+        } else if (D.Xf) {
+            KG_FOR(i) {
+                const double2 u = element(i);
+                D.Xf[i] = make_longlong2(fix_term(u.x, Ef, P, 0u), fix_term(u.y, Ef, P, 0u));
+            }
+        } else {
+            KG_FOR(i) I1[i] = fix_image(element(i), Ef);
         }
-        if (blk == 0 && threadIdx.x == 0) C->efix = Ef;
+        if (blk == 0 && threadIdx.x == 0) {
+            if (D.Xf) C->efix = Ef;
+            if (img) C->eimg[j + 1] = Ef;
+        }
     } else {
         KG_FOR(i) element(i);
     }
@@ -1152,8 +1383,10 @@ int prepare_step(Krylov& K, int reorth) {
     KG_TRY(work_list(K, (const void*)k_update, -1, &items, &n));
     if (reorth >= 1) {
         // every vector count of one step (and of the ground-state restarts)
-        for (int nk = 1; nk <= std::min(kChunk, K.M + 1); ++nk)
+        for (int nk = 1; nk <= std::min(kChunk, K.M + 1); ++nk) {
             KG_TRY(work_list(K, (const void*)dots_kernel(nk), -1, &items, &n));
+            if (use_int_dots(K, false)) KG_TRY(work_list(K, (const void*)int_dots_kernel(nk), -1, &items, &n));
+        }
     }
     const void* comb[4] = {(const void*)k_combine<0>, (const void*)k_combine<4>, (const void*)k_combine<12>,
                            (const void*)k_combine<32>};
@@ -1237,7 +1470,7 @@ int ground_state(kg_sector* s, const kg_opts* o) {
             break;
         }
         if ((rc = launch_scale_copy(s->gs, s->gs, d, 1.0 / h.ovnorm, st)) != KG_OK) break;
-        if ((rc = launch_hpsi(S, s->gs, W0, st)) != KG_OK) break;
+        if ((rc = launch_hpsi(s, s->gs, W0, st)) != KG_OK) break;
         k_rq<<<nrq, kThreads, 0, st>>>(s->gs, W0, d, K.cs, 0, part, K.cnt);
         count_launch();
         k_rq<<<nrq, kThreads, 0, st>>>(s->gs, W0, d, K.cs, 1, part, K.cnt);

@@ -354,6 +354,8 @@ void sector_free(kg_sector* s) {
     cudaFree(s->Utab);
     cudaFree(s->diag);
     cudaFree(s->gs);
+    cudaFree(s->hp_emax);
+    cudaFree(s->hp_xf);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->fence) cudaEventDestroy(s->fence);
     delete s;

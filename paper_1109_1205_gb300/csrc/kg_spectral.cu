@@ -37,7 +37,7 @@ struct LzCol {
 static int lanczos_columns(kg_sector* s, const int* orb, int n_orb, int n, const kg_opts* o, std::vector<LzCol>& cl,
                            std::vector<ColScalars>& h) {
     if (!orb || n_orb < 1 || n < 1 || n > kMaxMgs - 1 || o->reorth < 0 || o->reorth > 2 || o->schedule < 0 ||
-        o->schedule > 3) {
+        o->schedule > 7) {
         set_error("bad arguments to the Lanczos runs (need orbitals and 1 <= n <= %d)", kMaxMgs - 1);
         return KG_EINVAL;
     }
