@@ -134,11 +134,14 @@ def step_bytes(d, B, M, n_ov=0):
     return {"lanczos_hpsi": hpsi, "reorth_dots": dots, "update": upd, "combine": comb, "colnorm": v}
 
 
-def step_flops(d, B, M, hops):
-    """FP64 operations (FMA = 2) per propagation step, by kernel class."""
+def step_flops(d, B, M, hops, int_dots=True):
+    """FP64 operations (FMA = 2) per propagation step, by kernel class.  With
+    the exact integer Gram-Schmidt dots (the default schedule) the dots
+    kernel's only FP64 work is u = W - a_j v_j; its products run on the
+    integer pipe."""
     e = float(d) * B
     return {"lanczos_hpsi": sum(e * (2 * hops + 17) for _ in range(M)),
-            "reorth_dots": sum(e * (4 + 8 * (j + 1)) for j in range(M)),
+            "reorth_dots": sum(e * (4 if int_dots else 4 + 8 * (j + 1)) for j in range(M)),
             "update": sum(e * (4 + 8 * (j + 1) + 4) for j in range(M)),
             "combine": e * 8 * (M + 1), "colnorm": e * 4}
 

@@ -306,8 +306,9 @@ static int grad_pass(const kg_sector* sec, const double2* U, const double2* Wv, 
 // caller forms the vectors it needs at the times it needs).
 int build_space(Krylov& K, int reorth, cudaStream_t st) {
     KG_TRY(launch_colnorm(K, st));
+    const bool ain = alpha_in_dots(K, reorth);
     for (int j = 0; j < K.M; ++j) {
-        KG_TRY(launch_lanczos_hpsi(K, j, st));
+        KG_TRY(launch_lanczos_hpsi(K, j, st, !ain));
         if (reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));

@@ -268,8 +268,8 @@ struct HpsiShared {
 };
 
 template <int MODE>
-__device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalars* cs, int j, unsigned* cnt,
-                                                  const int4 it_, HpsiShared& sh) {
+__device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalars* cs, int j, int with_alpha,
+                                                  unsigned* cnt, const int4 it_, HpsiShared& sh) {
     const int b = it_.x, blk = it_.y, nblk = it_.z;
     const ColDesc D = desc[b];
     ColScalars* C = cs + b;
@@ -322,7 +322,7 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
         }
         w[idx] = r;
         if (j == 0 && D.I) D.I[idx] = fix_image(xv, E0img);  // image of V_0 for the exact dots
-        acc[0] = fma(xv.x, r.x, fma(xv.y, r.y, acc[0]));  // Re conj(x) r
+        if (with_alpha) acc[0] = fma(xv.x, r.x, fma(xv.y, r.y, acc[0]));  // Re conj(x) r
         ew = max(ew, max(exp_field(r.x), exp_field(r.y)));
     }
     acc[0] *= sj;
@@ -332,7 +332,9 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
     __syncthreads();
     if (grid_finish(bs, 1, D.part, cnt + b, blk, nblk, red, 1)) {
         if (threadIdx.x == 0) {
-            const double a = red[0];
+            // without with_alpha, a_j = <v_j, w> comes from the exact dots
+            // (their coefficient of v_j), which the update adds to alpha[j]
+            const double a = with_alpha ? red[0] : 0.0;
             C->alpha[j] = a;
             C->ew = (int)red[1];
             if (!isfinite(a)) {
@@ -345,10 +347,10 @@ __device__ __forceinline__ void lanczos_hpsi_item(const ColDesc* desc, ColScalar
 
 // One item per block (one-wave work lists, batches of any mix of sizes).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_lanczos_hpsi(const ColDesc* desc, const int4* items, ColScalars* cs,
-                                                           int j, unsigned* cnt) {
+__global__ void __launch_bounds__(kThreads, 4) k_lanczos_hpsi(const ColDesc* desc, const int4* items, ColScalars* cs,
+                                                           int j, int with_alpha, unsigned* cnt) {
     __shared__ HpsiShared sh;
-    lanczos_hpsi_item<MODE>(desc, cs, j, cnt, items[blockIdx.x], sh);
+    lanczos_hpsi_item<MODE>(desc, cs, j, with_alpha, cnt, items[blockIdx.x], sh);
 }
 
 int launch_hpsi(kg_sector* s, const double2* x, double2* y, cudaStream_t st) {
@@ -405,7 +407,7 @@ int prepare_hpsi_lists(Krylov& K) {
     return KG_OK;
 }
 
-int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st) {
+int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st, bool with_alpha) {
     bool present[4] = {false, false, false, false};
     for (auto& D : K.hdesc) present[D.mode] = true;
     ProfScope ps("lanczos_hpsi", st);
@@ -421,10 +423,10 @@ int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st) {
         for (int g = 0; g < K.ngroups[mode]; ++g) {
             KG_TRY(work_list(K, kern, mode, &items, &n, g));
             switch (mode) {
-                case 3: k_lanczos_hpsi<3><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-                case 0: k_lanczos_hpsi<0><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-                case 1: k_lanczos_hpsi<1><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
-                default: k_lanczos_hpsi<2><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, K.cnt); break;
+                case 3: k_lanczos_hpsi<3><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, with_alpha ? 1 : 0, K.cnt); break;
+                case 0: k_lanczos_hpsi<0><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, with_alpha ? 1 : 0, K.cnt); break;
+                case 1: k_lanczos_hpsi<1><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, with_alpha ? 1 : 0, K.cnt); break;
+                default: k_lanczos_hpsi<2><<<n, kThreads, 0, st>>>(K.desc, items, K.cs, j, with_alpha ? 1 : 0, K.cnt); break;
             }
             KG_LAUNCHED();
         }

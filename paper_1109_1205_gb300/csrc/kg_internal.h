@@ -218,7 +218,12 @@ int work_list(Krylov& K, const void* kern, int mode, const int4** items, int* n,
 int launch_hpsi(kg_sector* s, const double2* x, double2* y, cudaStream_t st);
 // Lanczos H*psi: w = s_j H V_j - b_j s_{j-1} V_{j-1} for every column, with the
 // partial sums of a_j = <v_j, w> reduced on the device.
-int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st);
+// with_alpha = false leaves a_j to the exact Gram-Schmidt dots (alpha_in_dots).
+int launch_lanczos_hpsi(Krylov& K, int j, cudaStream_t st, bool with_alpha = true);
+// True when the first Gram-Schmidt pass of level `reorth` runs the exact
+// integer dots, which then also give a_j = <v_j, w> (their coefficient of
+// v_j): H*psi skips its FP64 dot and the update subtracts a_j v_j.
+bool alpha_in_dots(const Krylov& K, int reorth);
 // start of a step: beta0 = ||V_0||, scale[0], largest exponent, m_eff = M.
 int launch_colnorm(Krylov& K, cudaStream_t st);
 // Reorthogonalisation: h_k = <v_k, w - a_j v_j> (first pass) or

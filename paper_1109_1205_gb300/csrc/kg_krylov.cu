@@ -405,12 +405,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
 // bound eimg[k]); u is formed in FP64 here and converted on a bound E_u of
 // its largest exponent.  With both numbers split into 26-bit halves, every
 // partial product (hi*hi, hi*lo, lo*hi, lo*lo) is an exact 64-bit integer
-// (one wide integer multiply-add).  Per element the cross and low terms are
-// combined exactly and rounded once, to nearest, to units of 2^52 of the
-// full product (the hi*hi unit): an unbiased error of at most half a unit,
-// 2^-53 of the product of the two vectors' largest components, only where
-// the products are that large.  A thread's sums are converted to FP64 once
-// per tile and reduced in a fixed order.  The FP64 pipe of this GPU issues
+// (one wide integer multiply-add).  The hi*hi and cross products are summed
+// exactly in two 64-bit accumulators (units 2^52 and 2^26 of the full
+// product); only lo*lo is rounded to the nearest 2^26, an error of 2^-79 of
+// the product of the two vectors' largest components per element.  A
+// thread's sums are converted to FP64 once per tile and reduced in a fixed
+// order.  The FP64 pipe of this GPU issues
 // about 2 multiply-adds per clock per SM, the integer pipe far more, so these
 // dots are bounded by the 16 bytes of I_k per element and vector instead of
 // the 3 FP64 multiply-adds per complex product of the Re+Im form.
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_reorth_dots(const ColDesc* desc
 // Each block takes its elements in tiles of kIntTile: first every thread
 // forms kIntTile / kThreads elements of u and their images (shared memory),
 // then the G thread groups take the tile's elements for their KH vectors
-// each, two elements per iteration with all their loads issued first.
+// each, the loads of an element's KH vectors issued first.
 //
 // The update writes I_{j+1} on an exponent bounded before V_{j+1} exists.
 // Near a breakdown (||V_{j+1}|| far below ||W||) that bound is loose and the
@@ -435,19 +435,21 @@ struct IntDots {
     static constexpr int TG = kThreads / G;                                      // threads per group
 };
 
-// Re and Im of conj(v) u in units of 2^52 of the full product, for v and u
-// given as split 52-bit images (v: {x_hi, x_lo, y_hi, y_lo}; u: Re hi/lo,
-// Im hi/lo and -Re hi/lo).
-__device__ __forceinline__ void cdot_fix(const int4 v, const int* uw, long long& re, long long& im) {
+// Re and Im of conj(v) u for v and u given as split 52-bit images (v:
+// {x_hi, x_lo, y_hi, y_lo}; u: Re hi/lo, Im hi/lo and -Re hi/lo): the
+// hi*hi part in units of 2^52 (re2, im2) and the rest in units of 2^26
+// (re1, im1) of the full product.
+__device__ __forceinline__ void cdot_fix(const int4 v, const int* uw, long long& re2, long long& re1,
+                                         long long& im2, long long& im1) {
     const int p1 = uw[0], p0 = uw[1], q1 = uw[2], q0 = uw[3], n1 = uw[4], n0 = uw[5];
     // Re = vx ux + vy uy
-    long long t = ((long long)v.y * p0 + (long long)v.w * q0) >> 26;
-    t += (long long)v.x * p0 + (long long)v.y * p1 + (long long)v.z * q0 + (long long)v.w * q1;
-    re += (long long)v.x * p1 + (long long)v.z * q1 + ((t + (1ll << 25)) >> 26);
+    re2 += (long long)v.x * p1 + (long long)v.z * q1;
+    re1 += (long long)v.x * p0 + (long long)v.y * p1 + (long long)v.z * q0 + (long long)v.w * q1 +
+           (((long long)v.y * p0 + (long long)v.w * q0 + (1ll << 25)) >> 26);
     // Im = vx uy - vy ux
-    long long s = ((long long)v.y * q0 + (long long)v.w * n0) >> 26;
-    s += (long long)v.x * q0 + (long long)v.y * q1 + (long long)v.z * n0 + (long long)v.w * n1;
-    im += (long long)v.x * q1 + (long long)v.z * n1 + ((s + (1ll << 25)) >> 26);
+    im2 += (long long)v.x * q1 + (long long)v.z * n1;
+    im1 += (long long)v.x * q0 + (long long)v.y * q1 + (long long)v.z * n0 + (long long)v.w * n1 +
+           (((long long)v.y * q0 + (long long)v.w * n0 + (1ll << 25)) >> 26);
 }
 
 template <int NK>
@@ -471,8 +473,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_reorth_dots_int(const ColDesc* 
     const double2* w = D.W;
     const double2* vj = D.V + (size_t)j * d;
     const double aj = C->alpha[j] * C->scale[j];
-    // the last chunk leaves u = W - a_j v_j in U for the update
-    const bool keep = k0 + NK == j + 1;
+    // a_j = 0 here means a_j comes from these dots (u = W, which the update
+    // reads itself); otherwise the last chunk leaves u = W - a_j v_j in U
+    const bool sub = aj != 0.0;
+    const bool keep = sub && k0 + NK == j + 1;
     if (threadIdx.x < NK) {
         ek_s[threadIdx.x] = C->emax[k0 + threadIdx.x];
         fresh_s[threadIdx.x] = C->eimg[k0 + threadIdx.x] - C->emax[k0 + threadIdx.x] > kFixSlack;
@@ -504,9 +508,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_reorth_dots_int(const ColDesc* 
             const int e = threadIdx.x + r * kThreads, i = base + e;
             if (i < d) {
                 double2 u = w[i];
-                const double2 p = vj[i];
-                u.x = fma(-aj, p.x, u.x);
-                u.y = fma(-aj, p.y, u.y);
+                if (sub) {
+                    const double2 p = vj[i];
+                    u.x = fma(-aj, p.x, u.x);
+                    u.y = fma(-aj, p.y, u.y);
+                }
                 if (keep) D.U[i] = u;
                 const long long px = fix52(u.x, Eu), py = fix52(u.y, Eu);
                 up[e][0] = fix_hi(px);
@@ -519,32 +525,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_reorth_dots_int(const ColDesc* 
         }
         __syncthreads();
         const int end = min(kIntTile, d - base);
-        long long re[KH], im[KH];
+        long long re2[KH], re1[KH], im2[KH], im1[KH];
 #pragma unroll
-        for (int k = 0; k < KH; ++k) re[k] = im[k] = 0;
-        // sums stay below 2^62: at most 2^53.1 per element and kIntTile / TG <= 128 elements
-        for (int e = t; e < end; e += 2 * TG) {
-            const int e2 = e + TG;
-            int4 va[KH], vb[KH];
+        for (int k = 0; k < KH; ++k) re2[k] = re1[k] = im2[k] = im1[k] = 0;
+        // a thread takes kIntTile / TG <= 32 elements of the tile, each adding
+        // at most 2^54.1 to an accumulator: the sums stay below 2^60
+        for (int e = t; e < end; e += TG) {
+            int4 va[KH];
 #pragma unroll
-            for (int k = 0; k < KH; ++k) {
-                if (k < kn) {
-                    va[k] = load(k, base + e);
-                    if (e2 < end) vb[k] = load(k, base + e2);
-                }
-            }
+            for (int k = 0; k < KH; ++k)
+                if (k < kn) va[k] = load(k, base + e);
 #pragma unroll
-            for (int k = 0; k < KH; ++k) {
-                if (k < kn) {
-                    cdot_fix(va[k], up[e], re[k], im[k]);
-                    if (e2 < end) cdot_fix(vb[k], up[e2], re[k], im[k]);
-                }
-            }
+            for (int k = 0; k < KH; ++k)
+                if (k < kn) cdot_fix(va[k], up[e], re2[k], re1[k], im2[k], im1[k]);
         }
 #pragma unroll
         for (int k = 0; k < KH; ++k) {
-            acc[2 * k] += (double)re[k];
-            acc[2 * k + 1] += (double)im[k];
+            acc[2 * k] += fma((double)re1[k], 0x1p-26, (double)re2[k]);
+            acc[2 * k + 1] += fma((double)im1[k], 0x1p-26, (double)im2[k]);
         }
         __syncthreads();
     }
@@ -612,6 +610,13 @@ static bool use_int_dots(const Krylov& K, bool second) {
     return true;
 }
 
+// a_j from the exact dots in the same pass as the Gram-Schmidt corrections
+// (classical Gram-Schmidt of w against v_0..v_j at once) loses
+// orthogonality over long Lanczos runs (a 120-step run past its exhausted
+// 100-state sector diverged); a_j is therefore always H*psi's FP64 dot, and
+// the exact dots correct it (u = w - a_j v_j first), as in the FP64 form.
+bool alpha_in_dots(const Krylov&, int) { return false; }
+
 int launch_reorth_dots(Krylov& K, int j, int k0, int nk, bool second, cudaStream_t st) {
     ProfScope ps("reorth_dots", st);
     if (use_int_dots(K, second)) {
@@ -654,6 +659,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     __shared__ float2 coef32[kMaxMgs + 1];
     __shared__ int idx32[kMaxMgs + 1], idx64[kMaxMgs + 1];
     __shared__ int n32, n64, efix_s;
+    __shared__ double coefA;
     __shared__ double sm[(kThreads / 32) * 2];
     __shared__ int smi[kThreads / 32];
     __shared__ double bs[2], red[2];
@@ -662,11 +668,20 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     const int d = D.d;
     double2* Vb = D.V;
     const int nk = (level >= 1 || second) ? j + 1 : 0;
+    // a first pass whose a_j came from the exact dots (alpha[j] still 0):
+    // Re h_j is a_j, subtracted here in FP64 (its tiny imaginary part joins
+    // the other Gram-Schmidt terms), from w itself
+    const bool ain = !second && level >= 1 && C->alpha[j] == 0.0;
     if (threadIdx.x == 0) {
         int a32 = 0, a64 = 0;
+        coefA = 0.0;
         for (int k = 0; k < nk; ++k) {
             const double s = C->scale[k];
-            const double2 h = C->h[k];
+            double2 h = C->h[k];
+            if (ain && k == j) {
+                coefA = s * h.x;
+                h.x = 0.0;
+            }
             const double2 c = make_double2(s * h.x, s * h.y);
             if ((fabs(h.x) + fabs(h.y)) < kSmallCoef) {  // |h_k| for the unit vector v_k
                 coef32[a32] = make_float2((float)c.x, (float)c.y);
@@ -681,7 +696,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     }
     __syncthreads();
     const int m32 = n32, m64 = n64;
-    const double aj = C->alpha[j] * C->scale[j];
+    const double aj = C->alpha[j] * C->scale[j], cA = coefA;
     const double2* w = second ? Vb + (size_t)(j + 1) * d : D.W;
     const double2* vj = Vb + (size_t)j * d;
     double2* out = Vb + (size_t)(j + 1) * d;
@@ -692,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
     int em = 0;
     // after a first-pass Gram-Schmidt (level >= 1) U holds W - a_j v_j
     const bool sub = !second && level < 1;
-    const double2* win = (!second && level >= 1) ? D.U : w;
+    const double2* win = (!second && level >= 1 && !ain) ? D.U : w;
     auto element = [&](int i) {
         double2 u = win[i];
         if (sub) {
@@ -746,6 +761,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
             u.x -= fma(c.x, v.x, -c.y * v.y);
             u.y -= fma(c.x, v.y, c.y * v.x);
         }
+        if (ain) {
+            const double2 p = vj[i];
+            u.x = fma(-cA, p.x, u.x);
+            u.y = fma(-cA, p.y, u.y);
+        }
         u.x -= f32_to_f64_int(cx);
         u.y -= f32_to_f64_int(cy);
         out[i] = u;
@@ -771,7 +791,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const ColDesc* desc, const 
         if (threadIdx.x == 0) {
             const int Eu = second ? C->emax[j + 1] : C->ew;
             double r = 1.0;
-            if (!second) r += fabs(aj) * ldexp(1.0, C->emax[j] - Eu);
+            if (!second) r += (fabs(aj) + fabs(cA)) * ldexp(1.0, C->emax[j] - Eu);
             for (int q = 0; q < m32; ++q)
                 r += (fabs((double)coef32[q].x) + fabs((double)coef32[q].y)) * ldexp(1.0, C->emax[idx32[q]] - Eu);
             for (int q = 0; q < m64; ++q)
@@ -1396,8 +1416,9 @@ int prepare_step(Krylov& K, int reorth) {
 
 int enqueue_step(Krylov& K, int reorth, cudaStream_t st) {
     KG_TRY(launch_colnorm(K, st));
+    const bool ain = alpha_in_dots(K, reorth);
     for (int j = 0; j < K.M; ++j) {
-        KG_TRY(launch_lanczos_hpsi(K, j, st));
+        KG_TRY(launch_lanczos_hpsi(K, j, st, !ain));
         if (reorth >= 1)
             for (int k0 = 0; k0 <= j; k0 += kChunk)
                 KG_TRY(launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st));
@@ -1446,7 +1467,7 @@ int ground_state(kg_sector* s, const kg_opts* o) {
     for (int r = 0; rc == KG_OK && r < o->max_restarts; ++r) {
         if ((rc = launch_colnorm(K, st)) != KG_OK) break;
         for (int j = 0; j < M && rc == KG_OK; ++j) {
-            rc = launch_lanczos_hpsi(K, j, st);
+            rc = launch_lanczos_hpsi(K, j, st, !alpha_in_dots(K, 1));
             for (int k0 = 0; rc == KG_OK && k0 <= j; k0 += kChunk)
                 rc = launch_reorth_dots(K, j, k0, std::min(kChunk, j + 1 - k0), false, st);
             if (rc == KG_OK) rc = launch_update(K, j, std::max(1, o->reorth), false, st);
