@@ -371,6 +371,25 @@ int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_
 int kg_keldysh_row(kg_keldysh* K, int k, double* G_les_kk, double* G_gtr_kk);
 int kg_keldysh_gram(kg_keldysh* K, double* G_les, double* G_gtr);
 int kg_keldysh_plan(const kg_keldysh* K, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
+/* ---- mixed components on the imaginary branch ---------------------------
+ * Section 4, the remark after step (iv): the components of the contour
+ * Green's function with one time on the imaginary branch, at zero
+ * temperature with the initial ground state |0> of H_ini and K = H_ini - mu N
+ * there (the imaginary time later on the contour):
+ *   G_right[k][j][a][a'] = G^right_{aa'}(t_k, tau_j) = +i <xi_a'(tau_j) | Psi_a(t_k)>,
+ *   G_left[j][k][a][a']  = G^left_{aa'}(tau_j, t_k)  = -i <zeta_a(tau_j) | chi_a'(t_k)>,
+ * xi_a(tau) = e^{-(H_ini - E0 + mu) tau} c_a|0>, zeta_a(tau) =
+ * e^{-(H_ini - E0 - mu) tau} c^dag_a|0> on tau_j = j dtau, j = 0..n_tau (the
+ * imaginary-time Krylov steps of kg_green_matsubara_steps, o->M vectors per
+ * step), and Psi_a, chi_a the step-(iii) columns of kg_green_keldysh on
+ * t_k = k dt, k < n_t.  G_right: host complex [n_t][n_tau+1][n_orb][n_orb];
+ * G_left: host complex [n_tau+1][n_t][n_orb][n_orb].  KG_EINVAL for bad
+ * arguments (as kg_green_keldysh, plus n_tau >= 0, finite dtau > 0 and mu),
+ * KG_ENOMEM when the Keldysh columns of all blocks do not fit together (see
+ * the memory plan below). */
+int kg_green_mixed(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t, double mu,
+                   double dtau, int n_tau, const kg_opts* o, double* G_right, double* G_left);
+
 /* Host copy of Phi(t_k) (complex, dimension d), and the reverse: replaces
  * the stored Phi(t_k) by a host vector (used to time a row end to end). */
 int kg_keldysh_get_phi(kg_keldysh* K, int k, double* phi_host);

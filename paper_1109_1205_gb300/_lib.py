@@ -73,6 +73,7 @@ _sig = {
     "kg_green_matsubara": (_I, [_P, _P, _I, _I, _D, _P, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_matsubara_steps": (_I, [_P, _P, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "kg_green_mixed": (_I, [_P, _P, _P, _I, _D, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
     "kg_keldysh_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -343,6 +344,18 @@ def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):
     _check(lib.kg_green_keldysh(h_ini, h_fin, orb.ctypes.data, n, float(dt), int(n_t), ctypes.byref(o),
                                 Gl.ctypes.data, Gg.ctypes.data), "kg_green_keldysh")
     return Gl, Gg
+
+
+def kg_green_mixed(h_ini, h_fin, orbitals, dt, n_t, mu, dtau, n_tau, opts=None):
+    """Mixed components (G_right [n_t, n_tau+1, n, n], G_left [n_tau+1, n_t, n, n])."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    Gr = np.zeros((n_t, n_tau + 1, n, n), dtype=np.complex128)
+    Gl = np.zeros((n_tau + 1, n_t, n, n), dtype=np.complex128)
+    _check(lib.kg_green_mixed(h_ini, h_fin, orb.ctypes.data, n, float(dt), int(n_t), float(mu), float(dtau),
+                              int(n_tau), ctypes.byref(o), Gr.ctypes.data, Gl.ctypes.data), "kg_green_mixed")
+    return Gr, Gl
 
 
 def kg_keldysh_create(h_ini, h_fin, orbitals, dt, n_t, opts=None):

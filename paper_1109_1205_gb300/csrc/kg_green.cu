@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -738,6 +739,72 @@ int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, do
     return release(KG_OK);
 }
 
+// The imaginary-time vectors of one (spin, kind) group of orbitals on
+// tau_j = j dtau, j = 0..n_steps: e^{-(H - s) tau_j} c_a|0> (dagger = 0,
+// s = E0 - mu) or e^{-(H - s) tau_j} c^dag_a|0> (dagger = 1, s = E0 + mu) in
+// the neighbour sector of H, by the imaginary-time Krylov steps of
+// green_matsubara_steps, each row copied to store[j][a][:].
+int imag_time_vectors(kg_sector* s, const int* orb, const std::vector<int>& idx, int spin, int dagger, double mu,
+                      double dtau, int n_steps, const kg_opts* o, double2* store, cudaStream_t st) {
+    kg_sector* nb = nullptr;
+    KG_TRY(neighbour(s, spin, dagger, &nb));
+    const int na = (int)idx.size(), dn = (int)nb->d;
+    std::vector<const kg_sector*> cols(na, nb);
+    Krylov K;
+    double2* cq = nullptr;
+    auto release = [&](int rc) {
+        cudaFree(cq);
+        krylov_free(K);
+        return rc;
+    };
+    const int rc_alloc = krylov_alloc(K, cols, std::min(o->M, dn), s->nsm, o->schedule);
+    if (rc_alloc != KG_OK) return release(rc_alloc);
+    if (cudaMalloc(&cq, sizeof(double2) * (size_t)na * K.M) != cudaSuccess) {
+        set_error("imaginary-time workspace allocation failed");
+        return release(KG_ENOMEM);
+    }
+    auto keep_row = [&](int j) -> int {
+        const cudaError_t e = cudaMemcpy2DAsync(store + (size_t)j * na * dn, (size_t)dn * sizeof(double2), K.vec(0, 0),
+                                                (size_t)(K.M + 1) * dn * sizeof(double2),
+                                                (size_t)dn * sizeof(double2), na, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? KG_OK : cuda_fail(e, "imaginary-time store", __FILE__, __LINE__);
+    };
+    for (int a = 0; a < na; ++a) {
+        const int rc = launch_cop(s, nb, orb[2 * idx[a]], spin, dagger, s->gs, K.vec(a, 0), st);
+        if (rc != KG_OK) return release(rc);
+    }
+    int rc = keep_row(0);
+    const double shift = dagger ? s->E0 + mu : s->E0 - mu;
+    std::vector<double2> hc((size_t)na * K.M);
+    std::vector<ColScalars> hcs(na);
+    for (int j = 1; rc == KG_OK && j <= n_steps; ++j) {
+        rc = build_space(K, o->reorth, st);
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(hcs.data(), K.cs, sizeof(ColScalars) * na, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "imaginary-time readback", __FILE__, __LINE__);
+        for (int a = 0; rc == KG_OK && a < na; ++a) {
+            if (hcs[a].status == KG_ENUMERIC) {
+                set_error("non-finite value during the imaginary-time steps");
+                rc = KG_ENUMERIC;
+                break;
+            }
+            imag_step_coefficients(hcs[a], shift, dtau, K.M, hc.data() + (size_t)a * K.M);
+        }
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(cq, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+             cudaMemcpy2DAsync(reinterpret_cast<char*>(K.cs) + offsetof(ColScalars, c), sizeof(ColScalars), cq,
+                               sizeof(double2) * K.M, sizeof(double2) * K.M, na, cudaMemcpyDeviceToDevice,
+                               st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "imaginary-time coefficients", __FILE__, __LINE__);
+        if (rc == KG_OK) rc = launch_combine(K, st);
+        if (rc == KG_OK) rc = keep_row(j);
+    }
+    if (rc == KG_OK && cudaStreamSynchronize(st) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "imaginary-time steps", __FILE__, __LINE__);
+    return release(rc);
+}
+
 }  // namespace kg
 
 // ------------------------------------------------------------- Keldysh
@@ -1195,6 +1262,83 @@ int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, dou
     return rc;
 }
 
+// Section 4, the remark after step (iv): the mixed components on the
+// imaginary branch at zero temperature, with the initial state |0> of H_ini
+// and K = H_ini - mu N there:
+//   G^right_{aa'}(t_k, tau_j) = +i <xi_a'(tau_j) | Psi_a(t_k)>,
+//   G^left_{aa'}(tau_j, t_k)  = -i <zeta_a(tau_j) | chi_a'(t_k)>,
+// xi_a(tau) = e^{-(H_ini - E0 + mu) tau} c_a|0>, zeta_a(tau) =
+// e^{-(H_ini - E0 - mu) tau} c^dag_a|0>, Psi and chi the step-(iii) columns
+// of the quench.  Rectangular overlaps of the stored imaginary-time vectors
+// (in the neighbour sectors of H_ini) with the stored Keldysh columns (the
+// same sectors of H_fin: the same basis).
+int green_mixed(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t, double mu, double dtau,
+                int n_tau, const kg_opts* o, double* G_right, double* G_left) {
+    if (!G_right || !G_left || n_tau < 0 || !(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(mu)) {
+        set_error("kg_green_mixed: need output buffers, n_tau >= 0, finite dtau > 0 and finite mu");
+        return KG_EINVAL;
+    }
+    kg_keldysh* X = nullptr;
+    KG_TRY(keldysh_create(ini, fin, orb, n_orb, dt, n_t, o, &X));
+    auto done = [&](int rc) {
+        keldysh_free(X);
+        return rc;
+    };
+    if (!X->keep_stores) {
+        set_error("kg_green_mixed needs every Keldysh column kept (they exceed the device-memory budget)");
+        return done(KG_ENOMEM);
+    }
+    for (int k = 0; k < n_t; ++k) {
+        const int rc = keldysh_row(X, k, nullptr, nullptr);
+        if (rc != KG_OK) return done(rc);
+    }
+    cudaStream_t st = pick_stream(fin, o);
+    const int nj = n_tau + 1, n = n_orb;
+    std::memset(G_right, 0, sizeof(double) * 2 * (size_t)n_t * nj * n * n);
+    std::memset(G_left, 0, sizeof(double) * 2 * (size_t)nj * n_t * n * n);
+    for (auto& B : X->blocks) {
+        const int na = (int)B.idx.size(), dn = (int)B.nb->d;
+        double2 *tau_store = nullptr, *ov = nullptr;
+        const int nx = nj * na, ny = n_t * na;
+        if (cudaMalloc(&tau_store, sizeof(double2) * (size_t)nx * dn) != cudaSuccess ||
+            cudaMalloc(&ov, sizeof(double2) * (size_t)nx * ny) != cudaSuccess) {
+            cudaFree(tau_store);
+            set_error("cannot hold the imaginary-time vectors of one block");
+            return done(KG_ENOMEM);
+        }
+        int rc = imag_time_vectors(ini, orb, B.idx, B.spin, B.dagger, mu, dtau, n_tau, o, tau_store, st);
+        // ov[y][x] = <tau vector x | Keldysh column y>, in chunks of kMaxOv tau vectors
+        for (int x0 = 0; rc == KG_OK && x0 < nx; x0 += kMaxOv)
+            rc = launch_inner_lib(tau_store + (size_t)x0 * dn, std::min(kMaxOv, nx - x0), B.store, ny, dn, ov + x0, nx,
+                                  st);
+        std::vector<double2> h((size_t)nx * ny);
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(h.data(), ov, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "mixed-component readback", __FILE__, __LINE__);
+        cudaFree(tau_store);
+        cudaFree(ov);
+        if (rc != KG_OK) return done(rc);
+        for (int k = 0; k < n_t; ++k)
+            for (int j = 0; j < nj; ++j)
+                for (int a = 0; a < na; ++a)
+                    for (int ap = 0; ap < na; ++ap) {
+                        if (!B.dagger) {  // G^right_{a a'}(t_k, tau_j) = i <xi_a'(tau_j) | Psi_a(t_k)>
+                            const double2 v = h[(size_t)(k * na + a) * nx + (j * na + ap)];
+                            const size_t off = (((size_t)k * nj + j) * n + B.idx[a]) * n + B.idx[ap];
+                            G_right[2 * off] = -v.y;
+                            G_right[2 * off + 1] = v.x;
+                        } else {  // G^left_{a a'}(tau_j, t_k) = -i <zeta_a(tau_j) | chi_a'(t_k)>
+                            const double2 v = h[(size_t)(k * na + ap) * nx + (j * na + a)];
+                            const size_t off = (((size_t)j * n_t + k) * n + B.idx[a]) * n + B.idx[ap];
+                            G_left[2 * off] = v.y;
+                            G_left[2 * off + 1] = -v.x;
+                        }
+                    }
+    }
+    return done(KG_OK);
+}
+
 }  // namespace kg
 
 extern "C" int kg_green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau,
@@ -1223,4 +1367,18 @@ extern "C" int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb
         return KG_EINVAL;
     }
     return kg::green_eq_batch(&s, 1, orb, n_orb, dt, n_steps, o, G_gtr, G_les, nullptr, false, fine);
+}
+
+extern "C" int kg_green_mixed(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
+                              double mu, double dtau, int n_tau, const kg_opts* o, double* G_right, double* G_left) {
+    if (!H_ini || !H_fin) {
+        kg::set_error("NULL sector");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    if (!o) {
+        kg_opts_default(&tmp);
+        o = &tmp;
+    }
+    return kg::green_mixed(H_ini, H_fin, orb, n_orb, dt, n_t, mu, dtau, n_tau, o, G_right, G_left);
 }

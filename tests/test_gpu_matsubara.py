@@ -96,3 +96,34 @@ def test_matsubara_steps_full_matrix(case):
     with pytest.raises(kg.KGError):
         s.green_matsubara_steps(orbs, mu, -0.1, 2)
     s.close()
+
+
+MIXED_CASES = {
+    # an interacting quench with complex hopping, orbitals of both spins
+    "interacting": (lambda: (W.random_model(4, 2, 1, seed=91, complex_hopping=True),
+                             W.random_model(4, 2, 1, seed=92, complex_hopping=True)),
+                    [(0, 0), (2, 0), (1, 1), (3, 1)], 0.1),
+    # the field quench of a 6-site SIAM chain (the paper's Section 4 setting)
+    "chain-field": (lambda: (W.siam_chain(6, 2.0, 3, 3, field=0.3), W.siam_chain(6, 2.0, 3, 3, field=0.0)),
+                    [(0, 0), (1, 0), (0, 1)], 0.0),
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED_CASES))
+def test_mixed_components_vs_oracle(name):
+    """G^right(t_k, tau_j) and G^left(tau_j, t_k) (Section 4, after step (iv))
+    from the stored imaginary-time vectors and Keldysh columns, against the
+    oracle's dense imaginary-time propagators and Chebyshev columns."""
+    make, orbs, mu = MIXED_CASES[name]
+    ini, fin = make()
+    dt, nt, dtau, ntau = 0.2, 5, 0.25, 8
+    si, sf = kg.Sector(ini), kg.Sector(fin)
+    Gr, Gl = kg.kg_green_mixed(si.handle, sf.handle, orbs, dt, nt, mu, dtau, ntau, kg.kg_opts_default(M=20))
+    rr, rl, _ = oracle.green_mixed(ini, fin, orbs, dt, nt, dtau * np.arange(ntau + 1), mu)
+    assert Gr.shape == rr.shape and Gl.shape == rl.shape
+    assert np.max(np.abs(Gr - rr)) < 1e-10 and np.max(np.abs(Gl - rl)) < 1e-10
+    # boundary: at t = 0 the real-time columns are c|0>, c^dag|0>, so
+    # G^left(tau, 0) = i G^M(tau) and G^right(0, tau) = i G^M(-tau)
+    Gp, Gm = si.green_matsubara_steps(orbs, mu, dtau, ntau, kg.kg_opts_default(M=20))
+    assert np.max(np.abs(Gl[:, 0] - 1j * Gp)) < 1e-10
+    assert np.max(np.abs(Gr[0] - 1j * Gm)) < 1e-10
