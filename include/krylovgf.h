@@ -264,7 +264,11 @@ int kg_green_matsubara(kg_sector* s, const int* orb, int n_orb, int n, double mu
  *   G_minus[k][a][b] = G^M_ab(-tau_k) = +<0| c^dag_b e^{-(H - E0 + mu) tau_k} c_a |0>,
  * host, complex [(n_steps+1)][n_orb][n_orb]; entries of opposite spins are
  * zero.  n_steps >= 0, dtau > 0 and mu finite (KG_EINVAL otherwise).  Runs
- * kg_ground_state first if needed. */
+ * kg_ground_state first if needed.  Every step checks the a-posteriori
+ * estimate b_M dtau |[e^{-(T - s) dtau} e_1]_{M-1}| of its relative error and
+ * returns KG_ENOCONV above 1e-11: the step must keep dtau times the spectral
+ * spread of H small against M (the error falls like (w dtau / 2)^M / M!, so
+ * for example M = 20 takes w dtau up to about 8). */
 int kg_green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau, int n_steps,
                              const kg_opts* o, double* G_plus, double* G_minus);
 

@@ -565,11 +565,13 @@ int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<doub
 // (substeps with ||T - s||_inf h <= 1/2, 18 terms).
 
 // Coefficients on the stored (unnormalised) basis: out[k] = beta0 scale_k
-// [e^{-(T - s) dtau} e_1]_k for k < m_eff, zero up to M.
-static void imag_step_coefficients(const ColScalars& c, double shift, double dtau, int M, double2* out) {
+// [e^{-(T - s) dtau} e_1]_k for k < m_eff, zero up to M.  Returns the usual
+// a-posteriori estimate of the step's relative error, b_m dtau
+// |[e^{-(T - s) dtau} e_1]_{m-1}| (zero when the space is invariant).
+static double imag_step_coefficients(const ColScalars& c, double shift, double dtau, int M, double2* out) {
     const int m = c.m_eff;
     for (int k = 0; k < M; ++k) out[k] = make_double2(0.0, 0.0);
-    if (m == 0) return;
+    if (m == 0) return 0.0;
     std::vector<double> v(m, 0.0), term(m), y(m), sum(m);
     v[0] = 1.0;
     double g = 0.0;
@@ -597,6 +599,20 @@ static void imag_step_coefficients(const ColScalars& c, double shift, double dta
         v = sum;
     }
     for (int k = 0; k < m; ++k) out[k] = make_double2(c.beta0 * c.scale[k] * v[k], 0.0);
+    if (m < M) return 0.0;  // happy breakdown: the Krylov space is invariant
+    double nv = 0.0;
+    for (int k = 0; k < m; ++k) nv += v[k] * v[k];
+    return c.beta[m] * dtau * std::fabs(v[m - 1]) / std::max(std::sqrt(nv), 1e-300);
+}
+
+// Largest accepted a-posteriori error of one imaginary-time Krylov step.
+constexpr double kImagStepTol = 1e-11;
+
+static int imag_step_error(double err, double dtau, int M) {
+    if (err <= kImagStepTol) return KG_OK;
+    set_error("imaginary-time Krylov step error estimate %.2e above %.0e: dtau = %g is too large for M = %d "
+              "(reduce dtau or raise M)", err, kImagStepTol, dtau, M);
+    return KG_ENOCONV;
 }
 
 int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau, int n_steps,
@@ -698,7 +714,8 @@ int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, do
                     return release(KG_ENUMERIC);
                 }
                 double2* c = hc.data() + (size_t)b * K.M;
-                imag_step_coefficients(hcs[b], shift, dtau, K.M, c);
+                const int erc = imag_step_error(imag_step_coefficients(hcs[b], shift, dtau, K.M, c), dtau, K.M);
+                if (erc != KG_OK) return release(erc);
                 for (int a = 0; a < na; ++a) {
                     std::complex<double> acc(0.0, 0.0);
                     for (int kk = 0; kk < m; ++kk) {
@@ -789,7 +806,8 @@ int imag_time_vectors(kg_sector* s, const int* orb, const std::vector<int>& idx,
                 rc = KG_ENUMERIC;
                 break;
             }
-            imag_step_coefficients(hcs[a], shift, dtau, K.M, hc.data() + (size_t)a * K.M);
+            rc = imag_step_error(imag_step_coefficients(hcs[a], shift, dtau, K.M, hc.data() + (size_t)a * K.M), dtau,
+                                 K.M);
         }
         if (rc == KG_OK &&
             (cudaMemcpyAsync(cq, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||

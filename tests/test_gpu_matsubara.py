@@ -127,3 +127,17 @@ def test_mixed_components_vs_oracle(name):
     Gp, Gm = si.green_matsubara_steps(orbs, mu, dtau, ntau, kg.kg_opts_default(M=20))
     assert np.max(np.abs(Gl[:, 0] - 1j * Gp)) < 1e-10
     assert np.max(np.abs(Gr[0] - 1j * Gm)) < 1e-10
+
+
+def test_matsubara_steps_reject_a_too_large_step():
+    """A step far beyond what its Krylov dimension resolves (M = 4, dtau = 2
+    on a star whose spectrum spans ~10) is refused by the step's error
+    estimate instead of returning an inaccurate G^M."""
+    cfg = W.config_c1()
+    s = kg.Sector(cfg["model"])
+    with pytest.raises(kg.KGError) as e:
+        s.green_matsubara_steps([(0, 0)], 0.0, 2.0, 3, kg.kg_opts_default(M=4))
+    assert e.value.code == kg.KG_ENOCONV and "too large" in kg.kg_last_error()
+    Gp, Gm = s.green_matsubara_steps([(0, 0)], 0.0, 0.25, 3, kg.kg_opts_default(M=20))
+    Rp, Rm, _ = oracle.green_matsubara(cfg["model"], [(0, 0)], 0.25 * np.arange(4), 0.0)
+    assert np.max(np.abs(Gp - Rp)) < 1e-10 and np.max(np.abs(Gm - Rm)) < 1e-10
