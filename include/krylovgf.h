@@ -214,6 +214,20 @@ int kg_green_equilibrium(kg_sector* s, const int* orb, int n_orb, double dt, int
 int kg_green_equilibrium_fine(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, int fine,
                               const kg_opts* o, double* G_gtr, double* G_les);
 
+/* ---- time-dependent Lanczos with restarts ------------------------------
+ * Section 3, Fig. 1 (Eqs. (newstate) and (udelta)): the equilibrium G of
+ * kg_green_equilibrium on t_k = k dt, k = 0..f*q, with one Krylov space of
+ * dimension n (full reorthogonalisation as opts->reorth) built every restart
+ * interval Delta t = q dt: inside an interval every output time comes from
+ * the same space through the eigen-decomposition of its tridiagonal matrix,
+ * and the state at the interval's end starts the next space.  f = 1 is the
+ * conventional Lanczos Green's function written in time (Eq. (res)); the
+ * paper's Fig. 1 uses n = 100, dt = 0.01, t_max = 1000 and f = 1, 100, 1000.
+ * 1 <= n <= 255, f >= 1, q >= 1, f*q <= 2^28, dt > 0 (KG_EINVAL otherwise).
+ * G_gtr, G_les: host, complex [(f*q+1)][n_orb][n_orb]. */
+int kg_green_restarted(kg_sector* s, const int* orb, int n_orb, int n, int f, int q, double dt, const kg_opts* o,
+                       double* G_gtr, double* G_les);
+
 /* ---- conventional Lanczos Green's function (frequency domain) ----------
  * Section 2, Eqs. (gomega), (resolv) and (gapprox): for each diagonal orbital
  * alpha = (site, spin), an n-step Lanczos run (full reorthogonalisation) from

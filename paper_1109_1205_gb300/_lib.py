@@ -74,6 +74,7 @@ _sig = {
     "kg_green_matsubara_steps": (_I, [_P, _P, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_mixed": (_I, [_P, _P, _P, _I, _D, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
+    "kg_green_restarted": (_I, [_P, _P, _I, _I, _I, _I, _D, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
     "kg_keldysh_gram": (_I, [_P, _P, _P]),
     "kg_keldysh_plan": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -346,6 +347,19 @@ def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):
     return Gl, Gg
 
 
+def kg_green_restarted(handle, orbitals, n, f, q, dt, opts=None):
+    """Equilibrium G^>, G^< on t_k = k dt, k = 0..f q, one Krylov space of
+    dimension n per interval of q steps; arrays [f q + 1, n_orb, n_orb]."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    m = orb.shape[0]
+    Gg = np.zeros((f * q + 1, m, m), dtype=np.complex128)
+    Gl = np.zeros_like(Gg)
+    _check(lib.kg_green_restarted(handle, orb.ctypes.data, m, int(n), int(f), int(q), float(dt), ctypes.byref(o),
+                                  Gg.ctypes.data, Gl.ctypes.data), "kg_green_restarted")
+    return Gg, Gl
+
+
 def kg_green_mixed(h_ini, h_fin, orbitals, dt, n_t, mu, dtau, n_tau, opts=None):
     """Mixed components (G_right [n_t, n_tau+1, n, n], G_left [n_tau+1, n_t, n, n])."""
     o = opts if opts is not None else kg_opts_default()
@@ -484,6 +498,9 @@ class Sector:
 
     def green_equilibrium(self, orbitals, dt, n_steps, opts=None):
         return kg_green_equilibrium(self.handle, orbitals, dt, n_steps, opts)
+
+    def green_restarted(self, orbitals, n, f, q, dt, opts=None):
+        return kg_green_restarted(self.handle, orbitals, n, f, q, dt, opts)
 
     def green_equilibrium_fine(self, orbitals, dt, n_steps, fine, opts=None):
         return kg_green_equilibrium_fine(self.handle, orbitals, dt, n_steps, fine, opts)

@@ -553,6 +553,227 @@ int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<doub
     return rc;
 }
 
+// ---------------------------- time-dependent Lanczos with f restarts
+// Eigen-decomposition of a real symmetric tridiagonal matrix by the implicit
+// QL method with Wilkinson-type shifts, eigenvectors accumulated by the
+// Givens rotations (Golub and Van Loan, Section 8.3).  d[0..m): diagonal,
+// e[0..m): e[k] couples k and k+1 (e[m-1] unused).  On return d holds the
+// eigenvalues and Z[k * m + j] the k-th component of eigenvector j.
+static void tql_eigen(std::vector<double>& d, std::vector<double>& e, int m, std::vector<double>& Z) {
+    Z.assign((size_t)m * m, 0.0);
+    for (int k = 0; k < m; ++k) Z[(size_t)k * m + k] = 1.0;
+    if (m > 0) e[m - 1] = 0.0;
+    const double eps = 2.220446049250313e-16;
+    for (int l = 0; l < m; ++l) {
+        for (int iter = 0; iter < 64; ++iter) {
+            int mm = l;
+            for (; mm < m - 1; ++mm)
+                if (std::fabs(e[mm]) <= eps * (std::fabs(d[mm]) + std::fabs(d[mm + 1]))) break;
+            if (mm == l) break;
+            // shift from the leading 2x2 block
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = mm - 1;
+            bool early = false;
+            for (; i >= l; --i) {
+                const double ff = s * e[i], b = c * e[i];
+                r = std::hypot(ff, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    e[mm] = 0.0;
+                    early = true;
+                    break;
+                }
+                s = ff / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                for (int k = 0; k < m; ++k) {
+                    double* row = Z.data() + (size_t)k * m;
+                    const double zf = row[i + 1];
+                    row[i + 1] = s * row[i] + c * zf;
+                    row[i] = c * row[i] - s * zf;
+                }
+            }
+            if (early) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[mm] = 0.0;
+        }
+    }
+}
+
+// Section 3, Fig. 1 and Eqs. (newstate), (udelta): the equilibrium G(t) on
+// t_k = k dt, k = 0..f q, with one Krylov space of dimension n per restart
+// interval Delta t = q dt.  Within an interval the space built from psi(t_r)
+// gives psi(t_r + tau) = ||psi|| V Z e^{-i Theta tau} Z^T e_1 (Eq. (udelta),
+// the eigen-decomposition T = Z Theta Z^T by implicit QL on the host) at
+// every output time, and psi(t_r + Delta t) starts the next space.  f = 1 is
+// the conventional Lanczos Green's function in the time domain (Eq. (res));
+// the paper's Fig. 1 compares f = 1, 100 and 1000 at n = 100.
+static int green_restarted(kg_sector* s, const int* orb, int n_orb, int n, int f, int q, double dt,
+                           const kg_opts* o, double* G_gtr, double* G_les) {
+    if (n < 1 || n > kMaxMgs - 1 || f < 1 || q < 1 || !(dt > 0.0) || !std::isfinite(dt) || !G_gtr || !G_les ||
+        (long long)f * q > (1ll << 28) || o->reorth < 0 || o->reorth > 2 || o->schedule < 0 || o->schedule > 7) {
+        set_error("kg_green_restarted: need 1 <= n <= %d, f, q >= 1, f q <= 2^28, finite dt > 0, outputs",
+                  kMaxMgs - 1);
+        return KG_EINVAL;
+    }
+    KG_TRY(check_orbitals(s, orb, n_orb));
+    const int rows = f * q + 1;
+    const size_t per = (size_t)rows * n_orb * n_orb * 2;
+    std::memset(G_gtr, 0, sizeof(double) * per);
+    std::memset(G_les, 0, sizeof(double) * per);
+    KG_TRY(ensure_gs(s, o));
+    std::vector<EqGroup> G;
+    std::vector<const kg_sector*> cols;
+    eq_groups(G, cols, s, 0, orb, n_orb);
+    if (cols.empty()) return KG_OK;
+    cudaStream_t st = pick_stream(s, o);
+    Krylov K;
+    double2 *P = nullptr, *cq = nullptr, *ov0 = nullptr;
+    auto release = [&](int rc) {
+        for (auto& g : G) cudaFree(g.chi);
+        cudaFree(P);
+        cudaFree(cq);
+        cudaFree(ov0);
+        krylov_free(K);
+        return rc;
+    };
+    int rc = krylov_alloc(K, cols, n, s->nsm, o->schedule);
+    if (rc != KG_OK) return release(rc);
+    const int B = K.B, MK = K.M + 1;
+    int na_max = 1;
+    size_t off = 0;
+    for (auto& g : G) {
+        const size_t na = g.idx.size();
+        na_max = std::max(na_max, (int)na);
+        g.ov0 = off;
+        off += na * rows * na;
+        if (cudaMalloc(&g.chi, sizeof(double2) * na * g.nb->d) != cudaSuccess) {
+            set_error("restarted-Lanczos workspace allocation failed");
+            return release(KG_ENOMEM);
+        }
+    }
+    if (cudaMalloc(&P, sizeof(double2) * (size_t)B * MK * na_max) != cudaSuccess ||
+        cudaMalloc(&cq, sizeof(double2) * (size_t)B * K.M) != cudaSuccess ||
+        cudaMalloc(&ov0, sizeof(double2) * (size_t)na_max * na_max) != cudaSuccess) {
+        set_error("restarted-Lanczos workspace allocation failed");
+        return release(KG_ENOMEM);
+    }
+    std::vector<double2> hov(off), h0((size_t)na_max * na_max);
+    for (auto& g : G) {
+        const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+        for (int a = 0; a < na && rc == KG_OK; ++a) {
+            rc = launch_cop(s, g.nb, orb[2 * g.idx[a]], g.spin, g.dagger, s->gs, g.chi + (size_t)a * dn, st);
+            if (rc == KG_OK &&
+                cudaMemcpyAsync(K.vec(g.col0 + a, 0), g.chi + (size_t)a * dn, sizeof(double2) * dn,
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = KG_ECUDA;
+        }
+        if (rc == KG_OK) rc = launch_inner_lib(g.chi, na, g.chi, na, dn, ov0, na, st);  // t = 0
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(h0.data(), ov0, sizeof(double2) * na * na, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "restarted Lanczos, t = 0", __FILE__, __LINE__);
+        if (rc != KG_OK) return release(rc);
+        for (int bcol = 0; bcol < na; ++bcol)
+            for (int a = 0; a < na; ++a) hov[g.ov0 + (size_t)bcol * rows * na + a] = h0[(size_t)bcol * na + a];
+    }
+    std::vector<double2> hP((size_t)B * MK * na_max), hc((size_t)B * K.M);
+    std::vector<ColScalars> hcs(B);
+    std::vector<double> dd, ee, Z;
+    std::vector<std::complex<double>> W, ph, step;
+    for (int r = 0; r < f; ++r) {
+        rc = build_space(K, o->reorth, st);
+        for (auto& g : G) {
+            const int na = (int)g.idx.size(), dn = (int)g.nb->d;
+            for (int a = 0; rc == KG_OK && a < na; ++a)
+                rc = launch_inner_lib(g.chi, na, K.vec(g.col0 + a, 0), MK, dn, P + (size_t)(g.col0 + a) * MK * na_max,
+                                      na_max, st);
+        }
+        if (rc == KG_OK &&
+            (cudaMemcpyAsync(hP.data(), P, sizeof(double2) * hP.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaMemcpyAsync(hcs.data(), K.cs, sizeof(ColScalars) * B, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = cuda_fail(cudaGetLastError(), "restarted-Lanczos readback", __FILE__, __LINE__);
+        if (rc != KG_OK) return release(rc);
+        for (auto& g : G) {
+            const int na = (int)g.idx.size();
+            const double sgn = g.dagger ? 1.0 : -1.0;  // particle columns forward, hole columns backward in t
+            for (int bcol = 0; bcol < na; ++bcol) {
+                const int b = g.col0 + bcol;
+                const ColScalars& c = hcs[b];
+                if (c.status == KG_ENUMERIC) {
+                    set_error("non-finite value in the restarted Lanczos run");
+                    return release(KG_ENUMERIC);
+                }
+                const int m = c.m_eff;
+                double2* cnext = hc.data() + (size_t)b * K.M;
+                for (int k = 0; k < K.M; ++k) cnext[k] = make_double2(0.0, 0.0);
+                if (m == 0) continue;  // the column vanished: G stays zero from here
+                dd.assign(c.alpha, c.alpha + m);
+                ee.assign(m, 0.0);
+                for (int k = 0; k + 1 < m; ++k) ee[k] = c.beta[k + 1];
+                tql_eigen(dd, ee, m, Z);
+                // G value of orbital a at tau: sum_m W[a][m] e^{-i theta_m sgn tau},
+                // W[a][m] = beta0 (sum_k <chi_a | V_k> s_k Z_km) Z_0m
+                W.assign((size_t)na * m, 0.0);
+                for (int a = 0; a < na; ++a)
+                    for (int mm = 0; mm < m; ++mm) {
+                        std::complex<double> acc(0.0, 0.0);
+                        for (int k = 0; k < m; ++k) {
+                            const double2 pv = hP[((size_t)b * MK + k) * na_max + a];
+                            acc += std::complex<double>(pv.x, pv.y) * (c.scale[k] * Z[(size_t)k * m + mm]);
+                        }
+                        W[(size_t)a * m + mm] = acc * (c.beta0 * Z[mm]);
+                    }
+                // output times t_r + i dt, i = 1..q: phases by repeated multiplication,
+                // re-anchored on exact values every 256 times
+                ph.assign(m, 1.0);
+                step.resize(m);
+                for (int mm = 0; mm < m; ++mm) step[mm] = std::polar(1.0, -dd[mm] * sgn * dt);
+                for (int i = 1; i <= q; ++i) {
+                    if ((i & 255) == 0)
+                        for (int mm = 0; mm < m; ++mm) ph[mm] = std::polar(1.0, -dd[mm] * sgn * dt * i);
+                    else
+                        for (int mm = 0; mm < m; ++mm) ph[mm] *= step[mm];
+                    const size_t row = (size_t)r * q + i;
+                    for (int a = 0; a < na; ++a) {
+                        std::complex<double> acc(0.0, 0.0);
+                        for (int mm = 0; mm < m; ++mm) acc += W[(size_t)a * m + mm] * ph[mm];
+                        hov[g.ov0 + ((size_t)bcol * rows + row) * na + a] = make_double2(acc.real(), acc.imag());
+                    }
+                }
+                // psi(t_r + Delta t) = V c, c_k = beta0 s_k sum_m Z_km e^{-i theta_m sgn q dt} Z_0m
+                for (int k = 0; k < m; ++k) {
+                    std::complex<double> acc(0.0, 0.0);
+                    for (int mm = 0; mm < m; ++mm)
+                        acc += Z[(size_t)k * m + mm] * std::polar(1.0, -dd[mm] * sgn * dt * q) * Z[mm];
+                    acc *= c.beta0 * c.scale[k];
+                    cnext[k] = make_double2(acc.real(), acc.imag());
+                }
+            }
+        }
+        if (r + 1 == f) break;
+        if (cudaMemcpyAsync(cq, hc.data(), sizeof(double2) * hc.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpy2DAsync(reinterpret_cast<char*>(K.cs) + offsetof(ColScalars, c), sizeof(ColScalars), cq,
+                              sizeof(double2) * K.M, sizeof(double2) * K.M, B, cudaMemcpyDeviceToDevice,
+                              st) != cudaSuccess)
+            return release(cuda_fail(cudaGetLastError(), "restarted-Lanczos coefficients", __FILE__, __LINE__));
+        rc = launch_combine(K, st);
+        if (rc != KG_OK) return release(rc);
+    }
+    for (auto& g : G) eq_assemble(g, hov, rows, dt, s->E0, n_orb, G_gtr, G_les);
+    return release(KG_OK);
+}
+
 // ------------------------------------------ Matsubara function on a tau grid
 // Section 4, after step (iv): the zero-temperature Matsubara function of H for
 // every orbital pair of one spin on tau_k = k dtau, by imaginary-time Krylov
@@ -1399,4 +1620,18 @@ extern "C" int kg_green_mixed(kg_sector* H_ini, kg_sector* H_fin, const int* orb
         o = &tmp;
     }
     return kg::green_mixed(H_ini, H_fin, orb, n_orb, dt, n_t, mu, dtau, n_tau, o, G_right, G_left);
+}
+
+extern "C" int kg_green_restarted(kg_sector* s, const int* orb, int n_orb, int n, int f, int q, double dt,
+                                  const kg_opts* o, double* G_gtr, double* G_les) {
+    if (!s) {
+        kg::set_error("NULL sector");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    if (!o) {
+        kg_opts_default(&tmp);
+        o = &tmp;
+    }
+    return kg::green_restarted(s, orb, n_orb, n, f, q, dt, o, G_gtr, G_les);
 }

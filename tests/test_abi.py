@@ -155,6 +155,7 @@ def test_every_handle_entry_rejects_null(kg):
     assert lib.kg_keldysh_gram(None, b, b) == E
     assert lib.kg_keldysh_plan(None, None, None, None, None) == E
     assert lib.kg_green_mixed(None, None, orb.ctypes.data, 1, 0.1, 1, 0.0, 0.1, 1, ob, b, b) == E
+    assert lib.kg_green_restarted(None, orb.ctypes.data, 1, 10, 1, 1, 0.1, ob, b, b) == E
     assert lib.kg_keldysh_get_phi(None, 0, b) == E
     assert lib.kg_keldysh_set_phi(None, 0, b) == E
     assert lib.kg_overlaps(None, 1, b, 1, 4, b, None) == E

@@ -102,3 +102,63 @@ def test_fourier_of_equilibrium_G_matches_oracle_chain():
         A = -(Fg[a] + Fl[a]).imag / np.pi
         assert np.min(A) > -1e-7  # e^{-eta t_max} truncation only
     s.close()
+
+
+# ------------------------- time-dependent Lanczos with restarts (Fig. 1)
+@pytest.mark.parametrize("f,q", [(1, 50), (5, 10)])
+def test_restarted_exhausted_space_is_exact(f, q):
+    """A Krylov space as large as the sector makes every interval exact: the
+    restarted G(t) equals the oracle's for one space or several."""
+    m = W.random_model(5, 2, 2, seed=37, complex_hopping=True)
+    orbs = [(0, 0), (3, 0), (1, 1)]
+    s = kg.Sector(m)
+    Gg, Gl = s.green_restarted(orbs, 120, f, q, 0.1)
+    rg, rl, _ = oracle.green_equilibrium(m, orbs, 0.1, f * q)
+    assert np.max(np.abs(Gg - rg)) < 1e-10 and np.max(np.abs(Gl - rl)) < 1e-10
+
+
+def test_restarted_short_intervals_vs_oracle():
+    """Intervals short enough for n = 30 (Delta t = 0.5 on the L = 8 ring,
+    output every 0.05): the restarted G(t) equals the oracle's to 1e-10."""
+    m = W.hubbard_ring(8, 4.0, 4, 4)
+    orbs = [(0, 0), (3, 0)]
+    s = kg.Sector(m)
+    Gg, Gl = s.green_restarted(orbs, 30, 8, 10, 0.05)
+    rg, rl, _ = oracle.green_equilibrium(m, orbs, 0.05, 80)
+    assert np.max(np.abs(Gg - rg)) < 1e-10 and np.max(np.abs(Gl - rl)) < 1e-10
+
+
+def test_restarted_single_space_is_the_lanczos_pole_sum():
+    """f = 1 (Eq. (res)): one Krylov space of n = 40 for the whole interval is
+    the n-pole conventional Lanczos function in time, built from the same
+    Lanczos coefficients that kg_green_lanczos returns."""
+    m = W.hubbard_ring(10, 8.0, 5, 5)
+    s = kg.Sector(m)
+    n, dt, q = 40, 0.05, 400
+    Gg, Gl = s.green_restarted([(0, 0)], n, 1, q, dt)
+    _, _, coef = s.green_lanczos([(0, 0)], n, np.zeros(1), 0.1)
+    E0, _, _ = s.ground_state()
+    t = dt * np.arange(q + 1)
+    for kind, G, sgn in ((0, Gg, 1.0), (1, Gl, -1.0)):
+        a, b = coef[0, kind, :n], coef[0, kind, n:]
+        mm = int(np.count_nonzero(a)) if np.any(a) else 0
+        T = np.diag(a[:mm]) + np.diag(b[1:mm], 1) + np.diag(b[1:mm], -1)
+        th, Z = np.linalg.eigh(T)
+        w = (b[0] * Z[0]) ** 2
+        # G^>(t) = -i sum w e^{-i(th - E0) t}; G^<(t) = +i sum w e^{+i(th - E0) t}
+        ref = (-1j if sgn > 0 else 1j) * np.exp(-1j * sgn * np.outer(t, th - E0)) @ w
+        assert np.max(np.abs(G[:, 0, 0] - ref)) < 1e-10
+
+
+def test_fig1_restart_comparison():
+    """Section 3, Fig. 1 on its own model (L = 10 ring, U = 8, half filling,
+    n = 100, t_max = 1000, dt' = 0.01, eta = 0.01): the converged spectrum
+    (f = 1000) and the conventional-Lanczos one (f = 1) are non-negative, the
+    f = 100 spectrum has negative weight, and both approximations deviate
+    from the converged one by a comparable amount."""
+    import bench
+    r = bench.fig1_restarts()
+    f1, f100, f1000 = r["f=1"], r["f=100"], r["f=1000"]
+    assert f1000["min_A"] > -1e-4 and f1["min_A"] > -1e-4
+    assert f100["min_A"] < -1e-2 and f100["negative_weight"] > 1e-3
+    assert 0.01 < f1["l1_to_f1000"] < 1.0 and 0.01 < f100["l1_to_f1000"] < 1.0
