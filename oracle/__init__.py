@@ -720,3 +720,102 @@ def green_equilibrium_dense(model, orbitals, dt, n_steps):
                 blk = 1j * np.einsum("bm,am,tm->tab", p.conj(), p, ph)
             G[np.ix_(range(n_steps + 1), idx, idx)] = blk
     return G_gtr, G_les, E0, gap
+
+
+# Fourth-order commutator-free exponential step with two exponentials (the
+# "higher-order commutator-free" propagators the outlook of the paper points
+# to): with A_1, A_2 the Hamiltonian at the Gauss nodes t + c_{1,2} h,
+# c_{1,2} = 1/2 -/+ sqrt(3)/6,
+#   U(t + h, t) = exp(-i h (a1 A_1 + a2 A_2)) exp(-i h (a2 A_1 + a1 A_2)),
+# a1 = (3 - 2 sqrt(3))/12, a2 = (3 + 2 sqrt(3))/12, the right factor first.
+CF4_A1 = (3.0 - 2.0 * np.sqrt(3.0)) / 12.0
+CF4_A2 = (3.0 + 2.0 * np.sqrt(3.0)) / 12.0
+CF4_C = (0.5 - np.sqrt(3.0) / 6.0, 0.5 + np.sqrt(3.0) / 6.0)
+
+
+def cf4_exponents(dparams):
+    """For each step the parameter offsets of the two exponentials' (halved)
+    Hamiltonians: a2 A_1 + a1 A_2 = H(fin + 2(a2 d_1 + a1 d_2)) / 2 (applied
+    first) and a1 A_1 + a2 A_2 = H(fin + 2(a1 d_1 + a2 d_2)) / 2, H being
+    linear in its parameters and a1 + a2 = 1/2.  dparams: [n_steps, 2, 3L]
+    (offsets of eps (spin-major, 2L) then U (L) at the two Gauss nodes)."""
+    d = np.asarray(dparams, dtype=np.float64)
+    first = 2.0 * (CF4_A2 * d[:, 0] + CF4_A1 * d[:, 1])
+    second = 2.0 * (CF4_A1 * d[:, 0] + CF4_A2 * d[:, 1])
+    return first, second
+
+
+def _shifted(model, dp):
+    L = model["L"]
+    m = dict(model)
+    m["eps"] = np.asarray(model["eps"], dtype=np.float64) + np.asarray(dp[:2 * L]).reshape(2, L)
+    m["U"] = np.asarray(model["U"], dtype=np.float64) + np.asarray(dp[2 * L:3 * L])
+    return m
+
+
+def green_keldysh_td(ini, fin, orbitals, dt, n_t, dparams, n_sub=1, gs=None, K=80, tol=1e-12):
+    """The Keldysh G^<, G^> of Section 4 (steps (i)-(iv), shaped like
+    green_keldysh) for a time-dependent Hamiltonian after the quench,
+    H(t) = H_fin + sum_{i sigma} de_{i sigma}(t) n_{i sigma} + sum_i dU_i(t)
+    n_{i up} n_{i dn}, each of the (n_t - 1) n_sub steps of h = dt / n_sub
+    propagated by the fourth-order commutator-free step above with every
+    exponential a Chebyshev expansion; dparams [(n_t-1) n_sub, 2, 3L] holds
+    the offsets at the two Gauss nodes of each step.  Phi(t_k) = U(t_k, 0)|0>,
+    Psi_a(t_k) = U(t_k, 0)^dag c_a Phi(t_k), chi_a likewise with c^dag."""
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    n_steps = (n_t - 1) * n_sub
+    h = dt / n_sub
+    first, second = cf4_exponents(np.asarray(dparams).reshape(n_steps, 2, -1)) if n_steps else ([], [])
+    cache = {}
+
+    def sector(dp, nu, nd):
+        key = (tuple(np.round(dp, 17)), nu, nd)
+        if key not in cache:
+            cache[key] = Sector(_shifted(fin, dp), nu, nd)
+        return cache[key]
+
+    def step(x, s, nu, nd, backward):
+        if not backward:  # U_s = e^{-i h/2 H2} e^{-i h/2 H1}
+            x = sector(first[s], nu, nd).propagate(x, 0.5 * h)
+            return sector(second[s], nu, nd).propagate(x, 0.5 * h)
+        # U_s^dag = e^{+i h/2 H1} e^{+i h/2 H2}
+        x = sector(second[s], nu, nd).propagate(x, -0.5 * h)
+        return sector(first[s], nu, nd).propagate(x, -0.5 * h)
+
+    nu0, nd0 = fin["n_up"], fin["n_dn"]
+    Phi = [psi0.copy()]
+    x = psi0.copy()
+    for s in range(n_steps):
+        x = step(x, s, nu0, nd0, False)
+        if (s + 1) % n_sub == 0:
+            Phi.append(x.copy())
+    sec_f = Sector(fin)
+    n = len(orbitals)
+    G_les = np.zeros((n_t, n_t, n, n), dtype=np.complex128)
+    G_gtr = np.zeros_like(G_les)
+    for spin, idx in _groups(orbitals).items():
+        if not idx:
+            continue
+        for dagger, G in ((False, G_les), (True, G_gtr)):
+            nb = sec_f.neighbour(spin, dagger)
+            if nb is None:
+                continue
+            vecs = []
+            for k in range(n_t):
+                row = []
+                for a in idx:
+                    v = sec_f.apply_cop(nb, orbitals[a][0], spin, dagger, Phi[k])
+                    for s in range(k * n_sub - 1, -1, -1):
+                        v = step(v, s, nb.n_up, nb.n_dn, True)
+                    row.append(v)
+                vecs.append(row)
+            for k in range(n_t):
+                for l in range(n_t):
+                    for ia, a in enumerate(idx):
+                        for ib, b in enumerate(idx):
+                            if not dagger:  # G^<_{ab}(t_k,t_l) = i <Psi_b(t_l)|Psi_a(t_k)>
+                                G[k, l, a, b] = 1j * np.vdot(vecs[l][ib], vecs[k][ia])
+                            else:  # G^>_{ab}(t_k,t_l) = -i <chi_a(t_k)|chi_b(t_l)>
+                                G[k, l, a, b] = -1j * np.vdot(vecs[k][ia], vecs[l][ib])
+    return G_les, G_gtr, E0

@@ -815,3 +815,112 @@ def test_dense_lehmann_route_equals_chebyshev_route(seed, L, nu, nd):
     assert np.max(np.abs(Gg - rg)) < 1e-11 and np.max(np.abs(Gl - rl)) < 1e-11
     if nu == L:
         assert np.all(Gg[:, :2, :2] == 0)
+
+
+# ------------------------------------------- time-dependent H(t) (Section 6)
+def _td_field(t, L):
+    """A smooth drive: every on-site energy and the impurity U oscillate."""
+    p = np.zeros(3 * L)
+    for s in range(2):
+        for i in range(L):
+            p[s * L + i] = 0.7 * np.sin(1.3 * t + 0.5 * i + 1.1 * s)
+    p[2 * L] = 0.8 * np.cos(2.1 * t)
+    return p
+
+
+def _td_dparams(field, dt, n_t, n_sub, L):
+    h = dt / n_sub
+    return np.array([[field(s * h + c * h, L) for c in oracle.CF4_C]
+                     for s in range((n_t - 1) * n_sub)])
+
+
+def _td_dense_reference(ini, fin, orbs, dt, nt, field, L, nu, nd):
+    """G^<, G^> from a dense Jordan-Wigner H(t) on the whole Fock space, the
+    propagator U(t, 0) integrated by scipy's DOP853 to 1e-13."""
+    import scipy.integrate as sint
+    c = jw_parts(L)
+    Hf = dense_fock_h(fin, c)
+    num = [c[q].T @ c[q] for q in range(2 * L)]
+    ops = num + [num[i] @ num[L + i] for i in range(L)]
+    dim = Hf.shape[0]
+
+    def rhs(t, y):
+        p = field(t, L)
+        H = Hf + sum(p[q] * ops[q] for q in range(3 * L))
+        return (-1j * (H @ y.reshape(dim, dim))).ravel()
+    sol = sint.solve_ivp(rhs, (0.0, dt * (nt - 1)), np.eye(dim, dtype=np.complex128).ravel(),
+                         method="DOP853", rtol=1e-13, atol=1e-14, t_eval=dt * np.arange(nt))
+    assert sol.status == 0
+    Us = [sol.y[:, k].reshape(dim, dim) for k in range(nt)]
+    Hi = dense_fock_h(ini, c)
+    i0 = sector_index(L, nu, nd)
+    w, v = np.linalg.eigh(Hi[np.ix_(i0, i0)])
+    g = np.zeros(dim, dtype=np.complex128)
+    g[i0] = v[:, 0]
+    n = len(orbs)
+    Rl = np.zeros((nt, nt, n, n), dtype=np.complex128)
+    Rg = np.zeros_like(Rl)
+    heis = [[Us[k].conj().T @ c[s * L + i] @ Us[k] for (i, s) in orbs] for k in range(nt)]
+    for k in range(nt):
+        for l in range(nt):
+            for a in range(n):
+                for b in range(n):
+                    ca, cbd = heis[k][a], heis[l][b].conj().T
+                    Rl[k, l, a, b] = 1j * (g.conj() @ cbd @ ca @ g)
+                    Rg[k, l, a, b] = -1j * (g.conj() @ ca @ cbd @ g)
+    return Rl, Rg
+
+
+def test_cf4_fourth_order_vs_dense_ode():
+    """The commutator-free step converges to the exact driven G with order
+    four (error ratio ~16 per halving of h); the exponentials in the other
+    order (a planted swap) fall to order two and fail this."""
+    L, nu, nd = 3, 2, 1
+    ini = W.siam_chain(L, 2.0, nu, nd, field=0.4)
+    fin = W.siam_chain(L, 2.0, nu, nd, field=0.0)
+    orbs = [(0, 0), (1, 0), (2, 1)]
+    dt, nt = 0.4, 5
+    Rl, Rg = _td_dense_reference(ini, fin, orbs, dt, nt, _td_field, L, nu, nd)
+    errs = []
+    for n_sub in (2, 4, 8):
+        Gl, Gg, _ = oracle.green_keldysh_td(ini, fin, orbs, dt, nt,
+                                            _td_dparams(_td_field, dt, nt, n_sub, L), n_sub=n_sub)
+        errs.append(max(np.max(np.abs(Gl - Rl)), np.max(np.abs(Gg - Rg))))
+    assert errs[-1] < 5e-8, errs
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 13.0 < e0 / e1 < 20.0, errs
+
+
+def test_cf4_constant_offsets_equal_the_shifted_quench():
+    """Offsets constant in time make every step exact: the driven G equals the
+    quench G of Section 4 with the offsets added to H_fin; a zero drive gives
+    the plain quench.  The sum rule holds at every time either way."""
+    L = 4
+    ini = W.siam_chain(L, 3.0, 2, 2, field=0.5)
+    fin = W.siam_chain(L, 3.0, 2, 2, field=0.0)
+    orbs = [(0, 0), (0, 1), (1, 1)]
+    dt, nt, n_sub = 0.3, 4, 3
+    p0 = _td_field(0.37, L)
+    dp = np.tile(p0, ((nt - 1) * n_sub, 2, 1))
+    Gl, Gg, _ = oracle.green_keldysh_td(ini, fin, orbs, dt, nt, dp, n_sub=n_sub)
+    Gl2, Gg2, _ = oracle.green_keldysh(ini, oracle._shifted(fin, p0), orbs, dt, nt)
+    assert rel(Gl, Gl2) < 1e-12 and rel(Gg, Gg2) < 1e-12
+    Gl0, Gg0, _ = oracle.green_keldysh_td(ini, fin, orbs, dt, nt, 0 * dp, n_sub=n_sub)
+    Gl3, Gg3, _ = oracle.green_keldysh(ini, fin, orbs, dt, nt)
+    assert rel(Gl0, Gl3) < 1e-12 and rel(Gg0, Gg3) < 1e-12
+    dp = _td_dparams(_td_field, dt, nt, n_sub, L)
+    Gl, Gg, _ = oracle.green_keldysh_td(ini, fin, orbs, dt, nt, dp, n_sub=n_sub)
+    for k in range(nt):
+        assert np.max(np.abs(1j * (np.diagonal(Gg[k, k]) - np.diagonal(Gl[k, k])) - 1.0)) < 1e-12
+    for G in (Gl, Gg):
+        assert np.max(np.abs(np.conj(G) + G.transpose(1, 0, 3, 2))) < 1e-12
+
+
+def test_cf4_nodes_and_weights():
+    """The two exponentials' weights sum to the step (a1 + a2 = 1/2 each) and
+    the nodes are the two-point Gauss-Legendre nodes on [0, 1]."""
+    assert abs(2 * (oracle.CF4_A1 + oracle.CF4_A2) - 1.0) < 1e-15
+    x, _ = np.polynomial.legendre.leggauss(2)
+    assert np.allclose(sorted(oracle.CF4_C), (x + 1) / 2, atol=1e-15)
+    first, second = oracle.cf4_exponents(np.array([[[1.0], [0.0]]]))
+    assert abs(first[0, 0] - 2 * oracle.CF4_A2) < 1e-15 and abs(second[0, 0] - 2 * oracle.CF4_A1) < 1e-15
