@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -311,7 +312,7 @@ def run_ours(args):
         cpu = cpu_baseline_sample(args.cpu_seconds)
 
     # ---- the batched and adjoint forms against the plain GPU path
-    batched = adjoint = spectral = c2_full = c3_row = None
+    batched = adjoint = spectral = c2_full = c3_row = driven = None
     if rank == 0 and world == 1 and not args.no_extras:
         batched = batched_vs_plain(args.batch_instances, args.batch_steps, args.plain_steps)
         adjoint = adjoint_vs_fd()
@@ -319,6 +320,7 @@ def run_ours(args):
         spectral["fine_grid"] = fine_grid_vs_plain(si, opts)
         spectral["fourier"] = fourier_transform(fp64)
         spectral["fig1"] = fig1_restarts()
+        driven = driven_vs_quench(si, sf, opts)
         if not args.no_c2_full:
             c2_full = c2_full_grid(si, sf, opts)
     if rank == 0 and world == 1 and args.c3:
@@ -339,6 +341,7 @@ def run_ours(args):
             "fp64_tflops_measured": round(fp64, 3), "cpu_baseline": cpu, "clocks": clocks,
             "setup_s": round(t_setup, 2), "E0_ini": E0, "gs_resid": res,
             "batched": batched, "adjoint": adjoint, "spectral": spectral, "c2_full": c2_full, "c3_row": c3_row,
+            "driven": driven,
         }
         print(json.dumps(line))
     if world > 1:
@@ -376,6 +379,58 @@ def c2_full_grid(si, sf, opts):
                         "step (iii), 1200-vector Gram per kind) through kg_green_keldysh",
             "seconds": round(sec, 2), "gsteps": gsteps, "gsteps_per_s": round(gsteps / sec, 1),
             "max_sum_rule_dev": sum_rule, "max_translation_dev": transl}
+
+
+# where the driven Keldysh calls sample the drive within an internal step h:
+# the two Gauss-Legendre nodes t + (1/2 -+ sqrt(3)/6) h (include/krylovgf.h)
+GAUSS2 = (0.5 - math.sqrt(3.0) / 6.0, 0.5 + math.sqrt(3.0) / 6.0)
+
+
+def driven_vs_quench(si, sf, opts, n_t=11):
+    """The c2 ring under a drive after the quench (every on-site energy
+    oscillating, U of site 0 modulated): the whole n_t x n_t grid for all 12
+    spin-up orbitals through kg_green_keldysh_td (fourth-order commutator-free
+    steps, two Krylov exponentials of dt/2 per step) against the undriven
+    quench through kg_green_keldysh on the same grid; then the order of the
+    driven steps at full size: the grid at t = 0.4 for h = 0.2, 0.1, 0.05
+    (self-convergence ratio |G_h - G_h/2| / |G_h/2 - G_h/4|, 16 for order 4)."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    cfg = W.config_c2()
+    orbs, dt = cfg["orbitals"], cfg["dt"]
+    f = W.periodic_drive(12)
+    dp = W.drive_samples(f, dt, n_t, 1, GAUSS2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gl, Gg = kg.kg_green_keldysh_td(si.handle, sf.handle, orbs, dt, n_t, dp, opts)
+    sec_td = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ql, Qg = kg.kg_green_keldysh(si.handle, sf.handle, orbs, dt, n_t, opts)
+    sec_q = time.perf_counter() - t0
+    gsteps = (n_t - 1) + 2 * len(orbs) * n_t * (n_t - 1) // 2
+    t = np.arange(n_t)
+    sum_rule = float(np.max(np.abs(1j * (Gg[t, t] - Gl[t, t]) - np.eye(len(orbs))[None])))
+    # self-convergence in h on a 3-point grid (t = 0, 0.2, 0.4), two orbitals
+    o2 = orbs[:2]
+    errs, grids = [], []
+    for n_sub in (1, 2, 4):
+        o = kg.kg_opts_default(M=opts.M, reorth=opts.reorth, dt_internal=0.2 / n_sub)
+        o.stream = opts.stream
+        grids.append(kg.kg_green_keldysh_td(si.handle, sf.handle, o2, 0.2, 3,
+                                            W.drive_samples(f, 0.2, 3, n_sub, GAUSS2), o))
+    for a, b in zip(grids, grids[1:]):
+        errs.append(float(max(np.max(np.abs(a[0] - b[0])), np.max(np.abs(a[1] - b[1])))))
+    return {"workload": "c2 ring (6,6) d=853776 after the U=8 -> 4 quench with a drive (eps_i(t) = 0.7 sin(1.3 t + "
+                        "phase), U_0(t) = 4 + 0.8 cos(2.1 t)); %dx%d grid, 12 spin-up orbitals, G^< and G^>, "
+                        "dt=0.05, M=20" % (n_t, n_t),
+            "seconds_driven": round(sec_td, 2), "seconds_quench": round(sec_q, 2), "gsteps": gsteps,
+            "gsteps_per_s_driven": round(gsteps / sec_td, 1), "gsteps_per_s_quench": round(gsteps / sec_q, 1),
+            "max_sum_rule_dev": sum_rule, "max_driven_minus_quench": float(np.max(np.abs(Gl - Ql))),
+            "self_convergence": {"h": [0.2, 0.1, 0.05], "diffs": errs,
+                                 "ratio": round(errs[0] / errs[1], 2) if errs[1] > 0 else None}}
 
 
 def c3_rows(n_t):
@@ -746,6 +801,7 @@ def main():
     ap.add_argument("--fig1-case", action="store_true", help="only the restarted-Lanczos comparison of Fig. 1")
     ap.add_argument("--fourier-case", action="store_true",
                     help="only the damped Fourier transform extra (for ncu captures of k_fourier)")
+    ap.add_argument("--driven-case", action="store_true", help="only the driven-H(t) extra on the c2 ring")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint comparisons")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=400)
@@ -759,6 +815,15 @@ def main():
         return
     if args.fig1_case:
         print(json.dumps({"fig1_case": fig1_restarts()}))
+        return
+    if args.driven_case:
+        import paper_1109_1205_gb300 as kg
+        import workloads as W
+        cfg = W.config_c2()
+        opts = kg.kg_opts_default(M=cfg["M"], reorth=1)
+        si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
+        si.ground_state(opts)
+        print(json.dumps({"driven_case": driven_vs_quench(si, sf, opts)}))
         return
     if args.fourier_case:
         import paper_1109_1205_gb300 as kg

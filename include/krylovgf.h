@@ -389,6 +389,33 @@ int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_
 int kg_keldysh_row(kg_keldysh* K, int k, double* G_les_kk, double* G_gtr_kk);
 int kg_keldysh_gram(kg_keldysh* K, double* G_les, double* G_gtr);
 int kg_keldysh_plan(const kg_keldysh* K, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
+/* ---- driven Hamiltonian after the quench ----------------------------------
+ * Section 6 (outlook): a Hamiltonian with a general time dependence after
+ * t = 0, propagated by a higher-order commutator-free exponential integrator.
+ * H(t) = H_fin + sum_{i,sigma} de_{i sigma}(t) n_{i sigma}
+ *              + sum_i dU_i(t) n_{i up} n_{i dn}
+ * (on-site energy and interaction offsets; hoppings fixed).  Every grid step
+ * is split into n_sub = max(1, round(dt / opts->dt_internal)) internal steps
+ * of h = dt / n_sub (n_sub = 1 when dt_internal <= 0), each propagated by the
+ * fourth-order commutator-free step with two exponentials,
+ *   U(t + h, t) = e^{-i h (a1 A_1 + a2 A_2)} e^{-i h (a2 A_1 + a1 A_2)},
+ * A_{1,2} = H(t + (1/2 -+ sqrt(3)/6) h), a1 = (3 - 2 sqrt(3))/12,
+ * a2 = (3 + 2 sqrt(3))/12 (right factor first), each exponential one Krylov
+ * step of h/2 with opts->M vectors; the error of G falls as h^4.
+ * dparams: host, [(n_t - 1) n_sub][2][3L] doubles: for internal step s and
+ * node j (the two times above, t = s h) the offsets de_{i up} (L values),
+ * de_{i dn} (L), dU_i (L).  It may be NULL only when n_t == 1.  G_les and
+ * G_gtr as in kg_green_keldysh, with Phi(t_k) = U(t_k, 0)|0>, Psi_a(t_k) =
+ * U(t_k, 0)^dag c_a Phi(t_k), chi_a(t_k) = U(t_k, 0)^dag c^dag_a Phi(t_k).
+ * Constant offsets reproduce kg_green_keldysh for H_fin with the offsets
+ * added.  KG_EINVAL for a non-finite offset or the kg_green_keldysh cases.
+ * kg_keldysh_create_td is the staged form (rows, Gram, plan, Phi as for
+ * kg_keldysh_create). */
+int kg_green_keldysh_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
+                        const double* dparams, const kg_opts* o, double* G_les, double* G_gtr);
+int kg_keldysh_create_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
+                         const double* dparams, const kg_opts* o, kg_keldysh** out);
+
 /* ---- mixed components on the imaginary branch ---------------------------
  * Section 4, the remark after step (iv): the components of the contour
  * Green's function with one time on the imaginary branch, at zero

@@ -73,6 +73,8 @@ _sig = {
     "kg_green_matsubara": (_I, [_P, _P, _I, _I, _D, _P, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_matsubara_steps": (_I, [_P, _P, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "kg_green_keldysh_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), _P, _P]),
+    "kg_keldysh_create_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_mixed": (_I, [_P, _P, _P, _I, _D, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_restarted": (_I, [_P, _P, _I, _I, _I, _I, _D, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_row": (_I, [_P, _I, _P, _P]),
@@ -347,6 +349,38 @@ def kg_green_keldysh(h_ini, h_fin, orbitals, dt, n_t, opts=None):
     return Gl, Gg
 
 
+def _dparams_array(dparams):
+    if dparams is None:
+        return None
+    return np.ascontiguousarray(np.asarray(dparams, dtype=np.float64))
+
+
+def kg_green_keldysh_td(h_ini, h_fin, orbitals, dt, n_t, dparams, opts=None):
+    """Keldysh G^<, G^> for the driven H(t): dparams [(n_t-1) n_sub, 2, 3L]
+    (offsets of eps_up, eps_dn, U at the two Gauss nodes of each internal step)."""
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    n = orb.shape[0]
+    dp = _dparams_array(dparams)
+    Gl = np.zeros((n_t, n_t, n, n), dtype=np.complex128)
+    Gg = np.zeros_like(Gl)
+    _check(lib.kg_green_keldysh_td(h_ini, h_fin, orb.ctypes.data, n, float(dt), int(n_t),
+                                   dp.ctypes.data if dp is not None and dp.size else None, ctypes.byref(o),
+                                   Gl.ctypes.data, Gg.ctypes.data), "kg_green_keldysh_td")
+    return Gl, Gg
+
+
+def kg_keldysh_create_td(h_ini, h_fin, orbitals, dt, n_t, dparams, opts=None):
+    o = opts if opts is not None else kg_opts_default()
+    orb = _orb_array(orbitals)
+    dp = _dparams_array(dparams)
+    out = _P()
+    _check(lib.kg_keldysh_create_td(h_ini, h_fin, orb.ctypes.data, orb.shape[0], float(dt), int(n_t),
+                                    dp.ctypes.data if dp is not None and dp.size else None, ctypes.byref(o),
+                                    ctypes.byref(out)), "kg_keldysh_create_td")
+    return out.value
+
+
 def kg_green_restarted(handle, orbitals, n, f, q, dt, opts=None):
     """Equilibrium G^>, G^< on t_k = k dt, k = 0..f q, one Krylov space of
     dimension n per interval of q steps; arrays [f q + 1, n_orb, n_orb]."""
@@ -532,11 +566,15 @@ class Sector:
 class Keldysh:
     """Staged four-step Keldysh calculation (create = steps (i)-(ii))."""
 
-    def __init__(self, ini, fin, orbitals, dt, n_t, opts=None):
+    def __init__(self, ini, fin, orbitals, dt, n_t, opts=None, dparams=None):
+        """dparams: the driven H(t) of kg_keldysh_create_td (None: the quench)."""
         self.n_orb = len(orbitals)
         self.n_t = n_t
         self.ini, self.fin = ini, fin  # the sectors must outlive this handle
-        self.handle = kg_keldysh_create(ini.handle, fin.handle, orbitals, dt, n_t, opts)
+        if dparams is None:
+            self.handle = kg_keldysh_create(ini.handle, fin.handle, orbitals, dt, n_t, opts)
+        else:
+            self.handle = kg_keldysh_create_td(ini.handle, fin.handle, orbitals, dt, n_t, dparams, opts)
 
     def row(self, k):
         return kg_keldysh_row(self.handle, k, self.n_orb)

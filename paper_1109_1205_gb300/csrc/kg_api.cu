@@ -200,6 +200,28 @@ int kg_green_keldysh(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_o
     return green_keldysh(H_ini, H_fin, orb, n_orb, dt, n_t, opts_or_default(o, &tmp), G_les, G_gtr);
 }
 
+int kg_green_keldysh_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
+                        const double* dparams, const kg_opts* o, double* G_les, double* G_gtr) {
+    if (!H_ini || !H_fin || (!dparams && n_t > 1)) {
+        set_error("NULL sector or drive");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    return green_keldysh(H_ini, H_fin, orb, n_orb, dt, n_t, opts_or_default(o, &tmp), G_les, G_gtr,
+                         n_t > 1 ? dparams : nullptr);
+}
+
+int kg_keldysh_create_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
+                         const double* dparams, const kg_opts* o, kg_keldysh** out) {
+    if (!H_ini || !H_fin || !out || (!dparams && n_t > 1)) {
+        set_error("NULL argument");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    return keldysh_create(H_ini, H_fin, orb, n_orb, dt, n_t, opts_or_default(o, &tmp), out,
+                          n_t > 1 ? dparams : nullptr);
+}
+
 int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
                       const kg_opts* o, kg_keldysh** out) {
     if (!H_ini || !H_fin || !out) {

@@ -1072,6 +1072,7 @@ struct KBlock {
     kg::Krylov K;
     kg::StepRunner R;
     bool ready = false;
+    double* dwork = nullptr;   // driven H(t): diagonal of the current exponential + tables
 };
 
 struct kg_keldysh {
@@ -1092,6 +1093,9 @@ struct kg_keldysh {
     size_t budget = 0;
     std::vector<KBlock> blocks;
     std::vector<char> row_done;
+    // driven H(t): per internal step the on-site offsets of its two
+    // exponentials, [(n_t - 1) n_sub][2][3L] on the device (null: a quench)
+    double* drive = nullptr;
 };
 
 namespace kg {
@@ -1106,9 +1110,67 @@ static void block_release(KBlock& B) {
     block_release_krylov(B);
     cudaFree(B.store);
     cudaFree(B.ovbuf);
+    cudaFree(B.dwork);
     B.store = nullptr;
     B.ovbuf = nullptr;
+    B.dwork = nullptr;
     B.slots = 0;
+}
+
+// ------------------------------------------------------- driven H(t)
+// Section 6 proposes commutator-free exponential propagators for a
+// Hamiltonian with a general time dependence after t = 0.  This build takes
+// the fourth-order one with two exponentials: with A_1, A_2 the Hamiltonian
+// at the two Gauss-Legendre nodes t + (1/2 -+ sqrt(3)/6) h of a step,
+//   U(t + h, t) = exp(-i h (a1 A_1 + a2 A_2)) exp(-i h (a2 A_1 + a1 A_2)),
+// a1 = (3 - 2 sqrt(3)) / 12, a2 = (3 + 2 sqrt(3)) / 12, the right factor
+// applied first.  The time dependence is an offset of the on-site energies
+// and U; H is linear in them and a1 + a2 = 1/2, so each exponential is
+// exp(-i (h/2) H(fin + o)) with o = 2 (a2 d_1 + a1 d_2) (first) or
+// 2 (a1 d_1 + a2 d_2) (second), d_1, d_2 the offsets at the nodes: a Krylov
+// step of tau = h/2 on a diagonal rebuilt before it.
+static const double kCF4_A1 = (3.0 - 2.0 * 1.7320508075688772) / 12.0;
+static const double kCF4_A2 = (3.0 + 2.0 * 1.7320508075688772) / 12.0;
+
+static size_t drive_bytes(const kg_keldysh* X, const kg_sector* s) {
+    return X->drive ? drive_work_doubles(s) * sizeof(double) : 0;
+}
+
+// Internal step `step` of the driven H(t) on every column of R (all in sector
+// s, whose diagonal the runner's columns read from `work`): forward
+// U = e^{-i h/2 H_2} e^{-i h/2 H_1}, or backward U^dag = e^{+i h/2 H_1}
+// e^{+i h/2 H_2}, the runner's tau being +h/2 or -h/2.
+static int driven_step(const kg_keldysh* X, const kg_sector* s, double* work, StepRunner& R, int step,
+                       bool backward, cudaStream_t st) {
+    const size_t L3 = 3 * (size_t)X->fin->L;
+    const double* first = X->drive + (size_t)step * 2 * L3;
+    const double* second = first + L3;
+    const SecView S = s->view();
+    KG_TRY(launch_drive_diag(S, backward ? second : first, work, st));
+    KG_TRY(R.run(st));
+    KG_TRY(launch_drive_diag(S, backward ? first : second, work, st));
+    return R.run(st);
+}
+
+// The exponentials' offsets from the offsets at the Gauss nodes (host
+// dparams [n_steps][2][3L]), uploaded to X->drive.
+static int drive_upload(kg_keldysh* X, const double* dparams, int n_steps) {
+    const size_t L3 = 3 * (size_t)X->fin->L;
+    std::vector<double> ex((size_t)n_steps * 2 * L3);
+    for (int s = 0; s < n_steps; ++s)
+        for (size_t p = 0; p < L3; ++p) {
+            const double d1 = dparams[((size_t)s * 2 + 0) * L3 + p], d2 = dparams[((size_t)s * 2 + 1) * L3 + p];
+            if (!std::isfinite(d1) || !std::isfinite(d2)) {
+                set_error("non-finite drive offset at step %d", s);
+                return KG_EINVAL;
+            }
+            ex[((size_t)s * 2 + 0) * L3 + p] = 2.0 * (kCF4_A2 * d1 + kCF4_A1 * d2);
+            ex[((size_t)s * 2 + 1) * L3 + p] = 2.0 * (kCF4_A1 * d1 + kCF4_A2 * d2);
+        }
+    if (ex.empty()) return KG_OK;
+    KG_CUDA(cudaMalloc(&X->drive, sizeof(double) * ex.size()));
+    KG_CUDA(cudaMemcpy(X->drive, ex.data(), sizeof(double) * ex.size(), cudaMemcpyHostToDevice));
+    return KG_OK;
 }
 
 static std::vector<const kg_sector*> block_cols(const KBlock& B) {
@@ -1132,8 +1194,20 @@ static int block_prepare(kg_keldysh* X, KBlock& B, cudaStream_t st, int slots, b
     if (!B.ovbuf) KG_CUDA(cudaMalloc(&B.ovbuf, sizeof(double2) * (size_t)na * na));
     if (B.ready) return KG_OK;
     KG_TRY(krylov_alloc(B.K, block_cols(B), std::min(X->o.M, dn), X->fin->nsm, X->o.schedule, planes));
-    for (auto& D : B.K.hdesc) D.tau = -X->dt / X->n_sub;  // step (iii) propagates backward, e^{+iH tau}
+    // step (iii) propagates backward, e^{+iH tau}; a driven H takes two
+    // exponentials of half the step each
+    const double tau = -X->dt / X->n_sub * (X->drive ? 0.5 : 1.0);
+    for (auto& D : B.K.hdesc) D.tau = tau;
     KG_TRY(krylov_upload(B.K, st));
+    if (X->drive) {
+        if (!B.dwork && cudaMalloc(&B.dwork, drive_bytes(X, B.nb)) != cudaSuccess) {
+            cudaGetLastError();
+            B.dwork = nullptr;
+            set_error("cannot hold the driven diagonal of dimension %d", dn);
+            return KG_ENOMEM;
+        }
+        KG_TRY(krylov_set_diag(B.K, B.dwork));
+    }
     KG_TRY(B.R.init(B.K, X->o.reorth, st, X->o.use_graphs != 0));
     B.ready = true;
     return KG_OK;
@@ -1164,7 +1238,11 @@ static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
     KG_TRY(launch_reset_status(B.K, st));
     for (int a = 0; a < na; ++a)
         KG_TRY(launch_cop(X->fin, B.nb, X->orb[2 * B.idx[a]], B.spin, B.dagger, phik, B.K.vec(a, 0), st));
-    for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));
+    if (X->drive) {
+        for (int n = k * X->n_sub - 1; n >= 0; --n) KG_TRY(driven_step(X, B.nb, B.dwork, B.R, n, true, st));
+    } else {
+        for (int n = 0; n < k * X->n_sub; ++n) KG_TRY(B.R.run(st));
+    }
     const int slot = B.slots > 1 ? k : 0;
     KG_CUDA(cudaMemcpy2DAsync(B.store + (size_t)slot * na * dn, (size_t)dn * sizeof(double2), B.K.vec(0, 0),
                               (size_t)(B.K.M + 1) * dn * sizeof(double2), (size_t)dn * sizeof(double2), na,
@@ -1172,16 +1250,18 @@ static int block_row(kg_keldysh* X, KBlock& B, int k, cudaStream_t st) {
     return KG_OK;
 }
 
-static int block_status(KBlock& B) {
-    std::vector<ColScalars> h(B.K.B);
-    KG_CUDA(cudaMemcpy(h.data(), B.K.cs, sizeof(ColScalars) * B.K.B, cudaMemcpyDeviceToHost));
+static int block_status_of(Krylov& K, const char* what) {
+    std::vector<ColScalars> h(K.B);
+    KG_CUDA(cudaMemcpy(h.data(), K.cs, sizeof(ColScalars) * K.B, cudaMemcpyDeviceToHost));
     for (auto& c : h)
         if (c.status == KG_ENUMERIC) {
-            set_error("non-finite value during step (iii)");
+            set_error("non-finite value during %s", what);
             return KG_ENUMERIC;
         }
     return KG_OK;
 }
+
+static int block_status(KBlock& B) { return block_status_of(B.K, "step (iii)"); }
 
 // Writes this block's part of G(t_k, t_l) for every stored k, l.
 static void block_assemble(kg_keldysh* X, KBlock& B, const std::vector<std::complex<double>>& Gm, double* G) {
@@ -1219,9 +1299,10 @@ static void plan_blocks(kg_keldysh* X) {
         const auto cols = block_cols(B);
         const int M = std::min(X->o.M, (int)B.nb->d);
         sum_store += (size_t)X->n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2);
-        sum_kry += krylov_bytes(cols, M, true);
-        max_kry = std::max(max_kry, krylov_bytes(cols, M, true));
-        max_kry_np = std::max(max_kry_np, krylov_bytes(cols, M, false));
+        const size_t dw = drive_bytes(X, B.nb);
+        sum_kry += krylov_bytes(cols, M, true) + dw;
+        max_kry = std::max(max_kry, krylov_bytes(cols, M, true) + dw);
+        max_kry_np = std::max(max_kry_np, krylov_bytes(cols, M, false) + dw);
     }
     const size_t B = X->budget;
     X->planes = true;
@@ -1235,7 +1316,7 @@ static void plan_blocks(kg_keldysh* X) {
 }
 
 int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
-                   const kg_opts* o, kg_keldysh** out) {
+                   const kg_opts* o, kg_keldysh** out, const double* dparams) {
     *out = nullptr;
     if (ini->L != fin->L || ini->nu != fin->nu || ini->nd != fin->nd) {
         set_error("H_ini and H_fin must share (L, N_up, N_dn)");
@@ -1263,6 +1344,10 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
         keldysh_free(X);
         return r;
     };
+    if (dparams) {
+        const int rc = drive_upload(X, dparams, (n_t - 1) * X->n_sub);
+        if (rc != KG_OK) return fail(rc);
+    }
     std::vector<int> idx[2];
     groups(orb, n_orb, idx);
     for (int spin = 0; spin < 2; ++spin) {
@@ -1285,11 +1370,13 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
     size_t block_peak = 0;
     for (auto& B : X->blocks)
         block_peak = std::max(block_peak, (size_t)n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2) +
-                                              krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), false));
+                                              krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), false) +
+                                              drive_bytes(X, B.nb));
     const int Mf = std::min(o->M, (int)d);
-    const bool fin_planes_dev = (size_t)n_t * d16 + krylov_bytes({fin}, Mf, true) <= X->budget;
+    const size_t fin_dw = drive_bytes(X, fin);
+    const bool fin_planes_dev = (size_t)n_t * d16 + krylov_bytes({fin}, Mf, true) + fin_dw <= X->budget;
     if ((size_t)n_t * d16 + block_peak <= X->budget &&
-        (size_t)n_t * d16 + krylov_bytes({fin}, Mf, false) <= X->budget) {
+        (size_t)n_t * d16 + krylov_bytes({fin}, Mf, false) + fin_dw <= X->budget) {
         if (cudaMalloc(&X->phi, sizeof(double2) * n_t * d) != cudaSuccess) {
             cudaGetLastError();
             X->phi = nullptr;
@@ -1322,22 +1409,36 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
     if (rc == KG_OK && n_t > 1) {
         Krylov K;
         StepRunner R;
+        double* work = nullptr;
         rc = krylov_alloc(K, {fin}, Mf, fin->nsm, o->schedule, X->phi ? fin_planes_dev : true);
         if (rc == KG_OK) {
-            K.hdesc[0].tau = dt / X->n_sub;
+            K.hdesc[0].tau = dt / X->n_sub * (X->drive ? 0.5 : 1.0);
             rc = krylov_upload(K, st);
+        }
+        if (rc == KG_OK && X->drive) {
+            if (cudaMalloc(&work, fin_dw) != cudaSuccess) {
+                cudaGetLastError();
+                work = nullptr;
+                set_error("cannot hold the driven diagonal of dimension %zu", d);
+                rc = KG_ENOMEM;
+            }
+            if (rc == KG_OK) rc = krylov_set_diag(K, work);
         }
         if (rc == KG_OK)
             rc = cudaMemcpyAsync(K.vec(0, 0), ini->gs, d16, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? KG_OK
                                                                                                          : KG_ECUDA;
         if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
+        if (rc == KG_OK) rc = launch_reset_status(K, st);
         for (int k = 1; rc == KG_OK && k < n_t; ++k) {
-            for (int n = 0; rc == KG_OK && n < X->n_sub; ++n) rc = R.run(st);
+            for (int n = 0; rc == KG_OK && n < X->n_sub; ++n)
+                rc = X->drive ? driven_step(X, fin, work, R, (k - 1) * X->n_sub + n, false, st) : R.run(st);
             if (rc == KG_OK) rc = put(k, K.vec(0, 0));
         }
         if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        if (rc == KG_OK) rc = block_status_of(K, "step (ii)");
         R.release();
         krylov_free(K);
+        cudaFree(work);
     } else if (rc == KG_OK) {
         rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
     }
@@ -1350,6 +1451,7 @@ int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, do
 void keldysh_free(kg_keldysh* X) {
     if (!X) return;
     for (auto& B : X->blocks) block_release(B);
+    cudaFree(X->drive);
     cudaFree(X->phi);
     cudaFree(X->phi_stage);
     if (X->phi_pinned)
@@ -1468,13 +1570,13 @@ int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* p
 // Whole Keldysh calculation, one (spin, kind) block at a time so that only
 // one block's stored columns and workspace are resident.
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
-                  const kg_opts* o, double* G_les, double* G_gtr) {
+                  const kg_opts* o, double* G_les, double* G_gtr, const double* dparams) {
     if (!G_les || !G_gtr) {
         set_error("NULL output");
         return KG_EINVAL;
     }
     kg_keldysh* X = nullptr;
-    KG_TRY(keldysh_create(ini, fin, orb, n_orb, dt, n_t, o, &X));
+    KG_TRY(keldysh_create(ini, fin, orb, n_orb, dt, n_t, o, &X, dparams));
     cudaStream_t st = pick_stream(fin, o);
     const size_t tot = (size_t)n_t * n_t * n_orb * n_orb * 2;
     std::memset(G_les, 0, sizeof(double) * tot);
@@ -1483,8 +1585,9 @@ int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, dou
     int rc = KG_OK;
     for (auto& B : X->blocks) {
         const size_t store = (size_t)n_t * B.idx.size() * (size_t)B.nb->d * sizeof(double2);
-        const bool planes =
-            phi_dev + store + krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), true) <= X->budget;
+        const bool planes = phi_dev + store + krylov_bytes(block_cols(B), std::min(o->M, (int)B.nb->d), true) +
+                                drive_bytes(X, B.nb) <=
+                            X->budget;
         rc = block_prepare(X, B, st, n_t, planes);
         for (int k = 0; rc == KG_OK && k < n_t; ++k) rc = block_row(X, B, k, st);
         if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;

@@ -188,6 +188,52 @@ int launch_diag_table(const SecView& S, double* diag, cudaStream_t st) {
     return KG_OK;
 }
 
+// Per-string and per-byte tables of a sector with on-site offsets added:
+// e_up'[i] = e_up[i] + sum over the set bits p of string i of dp[p] (spin up),
+// e_dn' likewise with dp[L + p], U'[c][v] = U[c][v] + sum over the set bits
+// b of byte v of dp[2L + 8c + b].  H is linear in eps and U, so the diagonal
+// built from these tables is that of the offset Hamiltonian.
+__global__ void k_drive_tables(SecView S, const double* dp, double* e_up, double* e_dn, double* utab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S.Du) {
+        double acc = S.up_e[i];
+        for (uint32_t b = S.up_bits[i]; b; b &= b - 1u) acc += dp[__ffs(b) - 1];
+        e_up[i] = acc;
+    }
+    if (i < S.Dd) {
+        double acc = S.dn_e[i];
+        for (uint32_t b = S.dn_bits[i]; b; b &= b - 1u) acc += dp[S.L + __ffs(b) - 1];
+        e_dn[i] = acc;
+    }
+    if (i < S.nchunk * 256) {
+        const int c = i >> 8;
+        double acc = S.Utab[i];
+        for (uint32_t b = (uint32_t)(i & 255); b; b &= b - 1u) {
+            const int site = 8 * c + __ffs(b) - 1;
+            if (site < S.L) acc += dp[2 * S.L + site];
+        }
+        utab[i] = acc;
+    }
+}
+
+size_t drive_work_doubles(const kg_sector* s) {
+    return (size_t)s->d + (size_t)s->Du + (size_t)s->Dd + (size_t)s->nchunk * 256;
+}
+
+int launch_drive_diag(const SecView& S, const double* dp, double* work, cudaStream_t st) {
+    double* e_up = work + S.d;
+    double* e_dn = e_up + S.Du;
+    double* utab = e_dn + S.Dd;
+    const int n = std::max(std::max(S.Du, S.Dd), S.nchunk * 256);
+    k_drive_tables<<<(n + 255) / 256, 256, 0, st>>>(S, dp, e_up, e_dn, utab);
+    KG_LAUNCHED();
+    SecView T = S;
+    T.up_e = e_up;
+    T.dn_e = e_dn;
+    T.Utab = utab;
+    return launch_diag_table(T, work, st);
+}
+
 // Largest exponent field over the components of x, into *emax (pre-set to 0).
 __global__ void __launch_bounds__(kThreads) k_maxexp(const double2* __restrict__ x, int d, int* emax) {
     __shared__ int sm[kThreads / 32];

@@ -237,6 +237,15 @@ int build_space(Krylov& K, int reorth, cudaStream_t st);
 // level: the reorthogonalisation level (0, 1, 2); second: the second pass.
 // diag[s] = e_up[i_up] + e_dn[i_dn] + sum of U over doubly occupied sites.
 int launch_diag_table(const SecView& S, double* diag, cudaStream_t st);
+// Driven Hamiltonians: work = [d] diagonal, then scratch tables (in doubles,
+// drive_work_doubles of them).  launch_drive_diag writes into work[0, d) the
+// diagonal of H with the on-site offsets dp = [eps_up (L), eps_dn (L), U (L)]
+// (device) added to the sector's eps and U.
+size_t drive_work_doubles(const kg_sector* s);
+int launch_drive_diag(const SecView& S, const double* dp, double* work, cudaStream_t st);
+// Points every column's sector view at `diag` (device, [d] of its sector),
+// before a StepRunner is initialised for K.
+int krylov_set_diag(Krylov& K, const double* diag);
 int launch_update(Krylov& K, int j, int level, bool second, cudaStream_t st);
 // Tridiagonal step: T = Q D Q^T on the device; mode 0: c = beta0 Q e^{-i D tau} Q^T e_1
 // with each column's tau; mode 1: ground-state Ritz pair (lam0, c = q_0).
@@ -300,15 +309,18 @@ int gram(const double2* X, int nv, int d, int nsm, std::vector<std::complex<doub
 int green_equilibrium_vjp(kg_sector* s, const int* orb, int n_orb, double dt, int n_steps, const kg_opts* o,
                           int checkpoint, const double* dGgtr, const double* dGles, double* g_eps, double* g_hre,
                           double* g_him, double* g_U);
+// dparams (host, or null for the quench): a driven H(t) after t = 0, the
+// on-site offsets at the Gauss nodes of every internal step,
+// [(n_t - 1) n_sub][2][3L] (eps_up, eps_dn, U).
 int keldysh_create(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
-                   const kg_opts* o, kg_keldysh** out);
+                   const kg_opts* o, kg_keldysh** out, const double* dparams = nullptr);
 void keldysh_free(kg_keldysh* X);
 int keldysh_row(kg_keldysh* X, int k, double* G_les_kk, double* G_gtr_kk);
 int keldysh_gram(kg_keldysh* X, double* G_les, double* G_gtr);
 int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in);
 int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
-                  const kg_opts* o, double* G_les, double* G_gtr);
+                  const kg_opts* o, double* G_les, double* G_gtr, const double* dparams = nullptr);
 int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o);
 void set_capturing(bool on);
 bool profiling();

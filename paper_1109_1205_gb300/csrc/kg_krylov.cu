@@ -175,6 +175,12 @@ int krylov_upload(Krylov& K, cudaStream_t st) {
     return KG_OK;
 }
 
+int krylov_set_diag(Krylov& K, const double* diag) {
+    for (auto& S : K.hsec) S.diag = diag;
+    KG_CUDA(cudaMemcpy(K.secs, K.hsec.data(), sizeof(SecView) * K.B, cudaMemcpyHostToDevice));
+    return KG_OK;
+}
+
 void krylov_free(Krylov& K) {
     for (auto& kv : K.lists) cudaFree(kv.second.first);
     cudaFree(K.Vbuf);

@@ -205,3 +205,29 @@ def random_state(d, seed):
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(d) + 1j * rng.standard_normal(d)
     return v / np.linalg.norm(v)
+
+
+def periodic_drive(L, amp_eps=0.7, omega=1.3, amp_U=0.8, omega_U=2.1, sites=None):
+    """A smooth drive of the on-site terms after the quench: returns f(t), the
+    offsets [eps_up (L), eps_dn (L), U (L)] at time t.  Every driven site's
+    energy oscillates with a site- and spin-dependent phase; U of site 0
+    oscillates too (a periodically modulated impurity).  sites: the driven
+    sites (default all)."""
+    sites = range(L) if sites is None else list(sites)
+
+    def f(t):
+        p = np.zeros(3 * L)
+        for s in range(2):
+            for i in sites:
+                p[s * L + i] = amp_eps * math.sin(omega * t + 0.5 * i + 1.1 * s)
+        p[2 * L] = amp_U * math.cos(omega_U * t)
+        return p
+    return f
+
+
+def drive_samples(f, dt, n_t, n_sub, nodes):
+    """The drive sampled where the driven Keldysh calls take it: for internal
+    step s (h = dt / n_sub, t_s = s h) and node c of `nodes` (fractions of
+    the step), f(t_s + c h); shape [(n_t - 1) n_sub, len(nodes), 3L]."""
+    h = dt / n_sub
+    return np.array([[f(s * h + c * h) for c in nodes] for s in range((n_t - 1) * n_sub)])
