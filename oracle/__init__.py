@@ -819,3 +819,56 @@ def green_keldysh_td(ini, fin, orbitals, dt, n_t, dparams, n_sub=1, gs=None, K=8
                             else:  # G^>_{ab}(t_k,t_l) = -i <chi_a(t_k)|chi_b(t_l)>
                                 G[k, l, a, b] = -1j * np.vdot(vecs[k][ia], vecs[l][ib])
     return G_les, G_gtr, E0
+
+
+def green_four_time(ini, fin, ops, dt, n_t, gs=None, K=80, tol=1e-12):
+    """Four-time correlation function of Section 6 (the outlook's higher-order
+    Green's functions) after the quench of Section 4:
+        G[k1, k2, k3, k4] = <0| A1(t1) A2(t2) A3(t3) A4(t4) |0>,  t_k = k dt,
+    A(t) = e^{iHt} A e^{-iHt} with H = H_fin, |0> the ground state of H_ini,
+    ops = four (site, spin, dagger) triples (dagger 1: c^dag, 0: c).  With
+    Phi(t) = e^{-iHt}|0>, the right vectors R(t3, t4) = e^{iH t3} A3
+    e^{-iH(t3 - t4)} A4 Phi(t4) and the left vectors L(t1, t2) = e^{iH t2}
+    A2^dag e^{-iH(t2 - t1)} A1^dag Phi(t1) live in one sector and
+    G = <L(t1, t2) | R(t3, t4)>; every exponential is one Chebyshev expansion.
+    Returns complex [n_t, n_t, n_t, n_t] (zero when the operators do not
+    conserve the particle numbers)."""
+    sec_i = Sector(ini)
+    E0, psi0, _ = sec_i.ground_state(K=K, tol=tol) if gs is None else gs
+    sec_f = Sector(fin)
+    Phi = [psi0.copy()]
+    for k in range(1, n_t):
+        Phi.append(sec_f.propagate(Phi[-1], dt))
+    G = np.zeros((n_t,) * 4, dtype=np.complex128)
+
+    def chain(first, second):
+        # sectors after `first` then `second` are applied to Phi's sector
+        s1 = sec_f.neighbour(first[1], bool(first[2]))
+        s2 = None if s1 is None else s1.neighbour(second[1], bool(second[2]))
+        return s1, s2
+
+    def pair_vectors(first, second):
+        # V[ta][tb] = e^{iH ta} B e^{-iH(ta - tb)} A Phi(tb), A = first, B = second
+        s1, s2 = chain(first, second)
+        if s2 is None:
+            return None, None
+        V = [[None] * n_t for _ in range(n_t)]
+        for tb in range(n_t):
+            v = sec_f.apply_cop(s1, first[0], first[1], bool(first[2]), Phi[tb])
+            for ta in range(n_t):
+                u = s1.propagate(v, (ta - tb) * dt)
+                w = s1.apply_cop(s2, second[0], second[1], bool(second[2]), u)
+                V[ta][tb] = s2.propagate(w, -ta * dt)
+        return (s2.n_up, s2.n_dn), V
+
+    a1, a2, a3, a4 = [tuple(int(v) for v in o) for o in ops]
+    key_r, R = pair_vectors(a4, a3)
+    key_l, Lv = pair_vectors((a1[0], a1[1], 1 - a1[2]), (a2[0], a2[1], 1 - a2[2]))
+    if R is None or Lv is None or key_r != key_l:
+        return G
+    for k1 in range(n_t):
+        for k2 in range(n_t):
+            for k3 in range(n_t):
+                for k4 in range(n_t):
+                    G[k1, k2, k3, k4] = np.vdot(Lv[k2][k1], R[k3][k4])
+    return G

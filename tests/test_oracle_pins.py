@@ -924,3 +924,79 @@ def test_cf4_nodes_and_weights():
     assert np.allclose(sorted(oracle.CF4_C), (x + 1) / 2, atol=1e-15)
     first, second = oracle.cf4_exponents(np.array([[[1.0], [0.0]]]))
     assert abs(first[0, 0] - 2 * oracle.CF4_A2) < 1e-15 and abs(second[0, 0] - 2 * oracle.CF4_A1) < 1e-15
+
+
+# ------------------------------------- four-time correlations (Section 6)
+FOUR_OPS = [[(0, 0, 0), (2, 1, 0), (1, 1, 1), (0, 0, 1)],   # c c c^dag c^dag, both spins
+            [(1, 0, 1), (1, 0, 0), (0, 1, 1), (2, 1, 0)],   # c^dag c c^dag c
+            [(0, 0, 1), (1, 0, 0), (2, 0, 1), (0, 0, 0)]]   # one spin: c^dag c c^dag c
+
+
+@pytest.mark.parametrize("ops", FOUR_OPS)
+def test_four_time_vs_dense_jordan_wigner(ops):
+    """<0|A1(t1) A2(t2) A3(t3) A4(t4)|0> after a field quench on L = 3 (U = 2)
+    against Heisenberg operators U^dag A U built from Jordan-Wigner matrices
+    and scipy expm on the 64-state Fock space, all 4^4 time combinations."""
+    L = 3
+    c = jw_parts(L)
+    ini = W.siam_chain(L, 2.0, 2, 1, field=0.4)
+    fin = W.siam_chain(L, 2.0, 2, 1, field=0.0)
+    dt, nt = 0.3, 4
+    G = oracle.green_four_time(ini, fin, ops, dt, nt)
+    Hi, Hf = dense_fock_h(ini, c), dense_fock_h(fin, c)
+    i0 = sector_index(L, 2, 1)
+    w, v = np.linalg.eigh(Hi[np.ix_(i0, i0)])
+    g = np.zeros(Hi.shape[0], dtype=np.complex128)
+    g[i0] = v[:, 0]
+    Us = [sla.expm(-1j * Hf * dt * k) for k in range(nt)]
+    mats = [c[s * L + i].T if dag else c[s * L + i] for (i, s, dag) in ops]
+    heis = [[Us[k].conj().T @ m @ Us[k] for k in range(nt)] for m in mats]
+    for k in np.ndindex(nt, nt, nt, nt):
+        ref = g.conj() @ heis[0][k[0]] @ heis[1][k[1]] @ heis[2][k[2]] @ heis[3][k[3]] @ g
+        assert abs(G[k] - ref) < 1e-12, (k, G[k], ref)
+    assert np.max(np.abs(G)) > 1e-2
+
+
+def test_four_time_free_fermions_wick():
+    """U = 0 quench of random complex hoppings (L = 5, (3, 2)): the four-time
+    function factorises by Wick's theorem into two-time functions
+    <c_x(t) c^dag_y(t')> = [u(t) (1 - rho) u(t')^dag]_xy of the single-particle
+    propagator u(t) = e^{-i h_f t} and the initial one-body density rho:
+    <c_a c_b c^dag_c c^dag_d> = <c_a c^dag_d><c_b c^dag_c> - <c_a c^dag_c><c_b c^dag_d>."""
+    L = 5
+    ini = W.random_model(L, 3, 2, seed=21, complex_hopping=True)
+    fin = W.random_model(L, 3, 2, seed=22, complex_hopping=True)
+    ini["U"][:] = 0.0
+    fin["U"][:] = 0.0
+    dt, nt = 0.25, 4
+    P = {}
+    for spin, N in ((0, 3), (1, 2)):
+        w, v = np.linalg.eigh(ini["h"] + np.diag(ini["eps"][spin]))
+        assert w[N] - w[N - 1] > 1e-3
+        rho = v[:, :N] @ v[:, :N].conj().T
+        hf = fin["h"] + np.diag(fin["eps"][spin])
+        u = [sla.expm(-1j * hf * dt * k) for k in range(nt)]
+        P[spin] = [[u[k] @ (np.eye(L) - rho) @ u[l].conj().T for l in range(nt)] for k in range(nt)]
+
+    def two(x, y, k, l):  # <c_x(t_k) c^dag_y(t_l)>
+        return P[x[1]][k][l][x[0], y[0]] if x[1] == y[1] else 0.0
+
+    for ops in ([(0, 0, 0), (3, 1, 0), (1, 1, 1), (4, 0, 1)], [(0, 0, 0), (2, 0, 0), (4, 0, 1), (1, 0, 1)]):
+        G = oracle.green_four_time(ini, fin, ops, dt, nt)
+        a, b, cc, d = ops
+        for k in np.ndindex(nt, nt, nt, nt):
+            ref = (two(a, d, k[0], k[3]) * two(b, cc, k[1], k[2]) - two(a, cc, k[0], k[2]) * two(b, d, k[1], k[3]))
+            assert abs(G[k] - ref) < 1e-12, (ops, k)
+
+
+def test_four_time_particle_number_selection():
+    """Operators that change the particle numbers give zero; a product with
+    A1 A2 = c_a c_a vanishes identically (Pauli)."""
+    L = 3
+    ini = W.siam_chain(L, 2.0, 2, 1, field=0.4)
+    fin = W.siam_chain(L, 2.0, 2, 1, field=0.0)
+    G = oracle.green_four_time(ini, fin, [(0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 0, 1)], 0.3, 3)
+    assert np.all(G == 0)
+    G = oracle.green_four_time(ini, fin, [(1, 0, 0), (1, 0, 0), (0, 0, 1), (2, 0, 1)], 0.3, 3)
+    for k in range(3):
+        assert np.max(np.abs(G[k, k])) < 1e-14
