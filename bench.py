@@ -306,6 +306,26 @@ def run_ours(args):
             "timing": "device time per call from CUDA events around its kernels; us_back_to_back includes "
                       "the host's issue time between calls"}
 
+    # ---- H*psi alone on a vector eleven times the L2 (the column sector of
+    # the 16-site chain, d = 91,611,520, 1.47 GB)
+    big = kg.Sector(W.with_sector(W.config_c3()["fin"], 6, 7))
+    xb = torch.randn(big.dim, dtype=torch.complex128, device="cuda")
+    yb = torch.empty_like(xb)
+    with torch.cuda.stream(stream):
+        big.hpsi(xb, yb, stream)
+        torch.cuda.synchronize()
+        kg.kg_profile_start()
+        for _ in range(5):
+            big.hpsi(xb, yb, stream)
+        bprof = kg.kg_profile_stop()
+    n_b, ms_b = bprof.get("hpsi", (1, float("nan")))
+    t_b = ms_b * 1e-3 / max(1, n_b)
+    hpsi["c3_column"] = {"d": big.dim, "us": round(t_b * 1e6, 1), "gbs": round(32.0 * big.dim / t_b / 1e9, 1),
+                         "frac_hbm": round(32.0 * big.dim / t_b / 1e9 / peaks["hbm_gbs"], 4),
+                         "algorithmic_bytes": 32 * big.dim}
+    del xb, yb, big
+    torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on the host cores, a bounded sample
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -321,6 +341,7 @@ def run_ours(args):
         spectral["fourier"] = fourier_transform(fp64)
         spectral["fig1"] = fig1_restarts()
         driven = driven_vs_quench(si, sf, opts)
+        driven["four_time"] = four_time(si, sf, opts)
         if not args.no_c2_full:
             c2_full = c2_full_grid(si, sf, opts)
     if rank == 0 and world == 1 and args.c3:
@@ -431,6 +452,33 @@ def driven_vs_quench(si, sf, opts, n_t=11):
             "max_sum_rule_dev": sum_rule, "max_driven_minus_quench": float(np.max(np.abs(Gl - Ql))),
             "self_convergence": {"h": [0.2, 0.1, 0.05], "diffs": errs,
                                  "ratio": round(errs[0] / errs[1], 2) if errs[1] > 0 else None}}
+
+
+def four_time(si, sf, opts, n_t=8):
+    """A four-time correlation function of the c2 quench (the higher-order
+    Green's functions of the paper's outlook): <0|c_0up(t1) c_1dn(t2)
+    c^dag_1dn(t3) c^dag_0up(t4)|0> on an n_t^4 grid at dt = 0.05 through
+    kg_green_four_time; the right and left two-time vector families of the
+    (7,7) sector and their n_t^2 x n_t^2 overlap matrix."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    ops = [(0, 0, 0), (1, 1, 0), (1, 1, 1), (0, 0, 1)]
+    dt = 0.05
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = kg.kg_green_four_time(si.handle, sf.handle, ops, dt, n_t, opts)
+    sec = time.perf_counter() - t0
+    per_family = n_t * (2 * (n_t - 1) + n_t * (n_t - 1) // 2)
+    gsteps = (n_t - 1) + 2 * per_family
+    eq = np.array([G[k, k, k, k] for k in range(n_t)])
+    return {"workload": "c2 ring after the U=8 -> 4 quench: <c_0up(t1) c_1dn(t2) c^dag_1dn(t3) c^dag_0up(t4)> "
+                        "on a %d^4 grid, dt=0.05, M=20 (two families of %d vectors in the (7,7) sector, "
+                        "d=627264)" % (n_t, n_t * n_t),
+            "seconds": round(sec, 2), "gsteps": gsteps, "gsteps_per_s": round(gsteps / sec, 1),
+            "equal_time_values": [round(float(v.real), 12) for v in eq],
+            "max_equal_time_imag": float(np.max(np.abs(eq.imag)))}
 
 
 def c3_rows(n_t):
@@ -823,7 +871,7 @@ def main():
         opts = kg.kg_opts_default(M=cfg["M"], reorth=1)
         si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
         si.ground_state(opts)
-        print(json.dumps({"driven_case": driven_vs_quench(si, sf, opts)}))
+        print(json.dumps({"driven_case": driven_vs_quench(si, sf, opts), "four_time": four_time(si, sf, opts)}))
         return
     if args.fourier_case:
         import paper_1109_1205_gb300 as kg

@@ -416,6 +416,24 @@ int kg_green_keldysh_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int 
 int kg_keldysh_create_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
                          const double* dparams, const kg_opts* o, kg_keldysh** out);
 
+/* ---- four-time correlation functions -------------------------------------
+ * Section 6 (outlook): higher-order Green's functions with four independent
+ * time arguments, by the Krylov steps of Section 4.  After the quench,
+ *   G[k1][k2][k3][k4] = <0| A1(t1) A2(t2) A3(t3) A4(t4) |0>,  t_k = k dt, k < n_t,
+ * A(t) = e^{iHt} A e^{-iHt} with H = H_fin, |0> the ground state of H_ini
+ * (H_ini = H_fin gives the equilibrium function).  ops: host, 12 ints, the
+ * four operators as (site, spin, dagger) with dagger 1 for c^dag, 0 for c.
+ * Computed as <L(t1,t2) | R(t3,t4)> with R = e^{iH t3} A3 e^{-iH(t3-t4)} A4
+ * Phi(t4) and L = e^{iH t2} A2^dag e^{-iH(t2-t1)} A1^dag Phi(t1), Phi(t) =
+ * e^{-iHt}|0>; every grid step is round(dt / opts->dt_internal) Krylov
+ * steps (one when dt_internal <= 0).  Device memory: Phi on n_t times and
+ * 2 n_t^2 vectors of the target sector, plus Krylov workspaces of n_t
+ * columns (KG_ENOMEM when they do not fit).  G: host complex [n_t]^4,
+ * zero when the operators change the particle numbers.  KG_EINVAL for a bad
+ * operator, n_t < 1, negative or non-finite dt, or sectors that differ. */
+int kg_green_four_time(kg_sector* H_ini, kg_sector* H_fin, const int* ops, double dt, int n_t, const kg_opts* o,
+                       double* G);
+
 /* ---- mixed components on the imaginary branch ---------------------------
  * Section 4, the remark after step (iv): the components of the contour
  * Green's function with one time on the imaginary branch, at zero

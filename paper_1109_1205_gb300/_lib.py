@@ -74,6 +74,7 @@ _sig = {
     "kg_green_matsubara_steps": (_I, [_P, _P, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_keldysh_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), _P, _P]),
+    "kg_green_four_time": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Opts), _P]),
     "kg_keldysh_create_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_mixed": (_I, [_P, _P, _P, _I, _D, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_restarted": (_I, [_P, _P, _I, _I, _I, _I, _D, ctypes.POINTER(Opts), _P, _P]),
@@ -368,6 +369,17 @@ def kg_green_keldysh_td(h_ini, h_fin, orbitals, dt, n_t, dparams, opts=None):
                                    dp.ctypes.data if dp is not None and dp.size else None, ctypes.byref(o),
                                    Gl.ctypes.data, Gg.ctypes.data), "kg_green_keldysh_td")
     return Gl, Gg
+
+
+def kg_green_four_time(h_ini, h_fin, ops, dt, n_t, opts=None):
+    """<0|A1(t1) A2(t2) A3(t3) A4(t4)|0> on t_k = k dt: ops = four (site, spin,
+    dagger) triples; returns complex [n_t, n_t, n_t, n_t]."""
+    o = opts if opts is not None else kg_opts_default()
+    op = np.ascontiguousarray(np.asarray(ops, dtype=np.int32).reshape(12))
+    G = np.zeros((n_t,) * 4, dtype=np.complex128)
+    _check(lib.kg_green_four_time(h_ini, h_fin, op.ctypes.data, float(dt), int(n_t), ctypes.byref(o),
+                                  G.ctypes.data), "kg_green_four_time")
+    return G
 
 
 def kg_keldysh_create_td(h_ini, h_fin, orbitals, dt, n_t, dparams, opts=None):

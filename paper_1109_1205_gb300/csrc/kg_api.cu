@@ -222,6 +222,16 @@ int kg_keldysh_create_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int
                           n_t > 1 ? dparams : nullptr);
 }
 
+int kg_green_four_time(kg_sector* H_ini, kg_sector* H_fin, const int* ops, double dt, int n_t, const kg_opts* o,
+                       double* G) {
+    if (!H_ini || !H_fin) {
+        set_error("NULL sector");
+        return KG_EINVAL;
+    }
+    kg_opts tmp;
+    return green_four_time(H_ini, H_fin, ops, dt, n_t, opts_or_default(o, &tmp), G);
+}
+
 int kg_keldysh_create(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int n_orb, double dt, int n_t,
                       const kg_opts* o, kg_keldysh** out) {
     if (!H_ini || !H_fin || !out) {

@@ -1681,6 +1681,202 @@ int green_mixed(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, doubl
     return done(KG_OK);
 }
 
+
+// ------------------------------------------- four-time correlation functions
+// Section 6 (outlook): functions of four time arguments, as the
+// nonequilibrium dual-fermion approach needs them, by the same Krylov steps.
+//   G(t1, t2, t3, t4) = <0| A1(t1) A2(t2) A3(t3) A4(t4) |0>,  A(t) = e^{iHt} A e^{-iHt},
+// H = H_fin, |0> the ground state of H_ini.  With Phi(t) = e^{-iHt}|0> this
+// is <L(t1, t2) | R(t3, t4)> for the right vectors
+//   R(t3, t4) = e^{iH t3} A3 e^{-iH(t3 - t4)} A4 Phi(t4)
+// and the left vectors L(t1, t2) = e^{iH t2} A2^dag e^{-iH(t2 - t1)} A1^dag Phi(t1),
+// both in the sector two operators away from H_fin's.  Each family is made
+// by pair_vectors: one batch of n_t columns A Phi(t_b) swept forward and
+// backward over the grid (every t_a - t_b), B applied at each grid point, and
+// the results brought back by e^{iH t_a} in batches of equal t_a.
+struct FourOp {
+    int site, spin, dagger;
+};
+
+// n grid steps of the runner's sign on every column: n_sub Krylov steps each.
+static int grid_steps(StepRunner& R, int n, int n_sub, cudaStream_t st) {
+    for (int k = 0; k < n * n_sub; ++k) KG_TRY(R.run(st));
+    return KG_OK;
+}
+
+// V[ta * n_t + tb] = e^{iH ta} B e^{-iH(ta - tb)} A Phi(tb) in sector s2.
+static int pair_vectors(kg_sector* fin, kg_sector* s1, kg_sector* s2, FourOp A, FourOp B, const double2* phi, int n_t,
+                        double dt, int n_sub, const kg_opts* o, double2* V, cudaStream_t st) {
+    const size_t d0 = (size_t)fin->d, d1 = (size_t)s1->d, d2 = (size_t)s2->d;
+    const double h = dt / n_sub;
+    int rc = KG_OK;
+    {
+        // every t_a - t_b: the columns A Phi(t_b) forward, then again backward
+        Krylov K;
+        StepRunner R;
+        rc = krylov_alloc(K, std::vector<const kg_sector*>(n_t, s1), std::min(o->M, (int)d1), fin->nsm, o->schedule);
+        for (int sweep = 0; rc == KG_OK && sweep < 2; ++sweep) {
+            const int sgn = sweep == 0 ? 1 : -1;
+            for (auto& D : K.hdesc) D.tau = sgn * h;
+            rc = krylov_upload(K, st);
+            if (rc == KG_OK && sweep == 0) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
+            if (rc == KG_OK) rc = launch_reset_status(K, st);
+            for (int tb = 0; rc == KG_OK && tb < n_t; ++tb)
+                rc = launch_cop(fin, s1, A.site, A.spin, A.dagger, phi + tb * d0, K.vec(tb, 0), st);
+            for (int m = sweep; rc == KG_OK && m < n_t; ++m) {
+                if (m > 0) rc = grid_steps(R, 1, n_sub, st);
+                for (int tb = 0; rc == KG_OK && tb < n_t; ++tb) {
+                    const int ta = tb + sgn * m;
+                    if (ta < 0 || ta >= n_t) continue;
+                    rc = launch_cop(s1, s2, B.site, B.spin, B.dagger, K.vec(tb, 0), V + ((size_t)ta * n_t + tb) * d2,
+                                    st);
+                }
+            }
+            if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+            if (rc == KG_OK) rc = block_status_of(K, "the four-time sweeps");
+        }
+        R.release();
+        krylov_free(K);
+    }
+    if (rc != KG_OK || n_t < 2) return rc;
+    // e^{iH t_a} on the n_t vectors of each t_a (t_a = 0 needs none)
+    Krylov K;
+    StepRunner R;
+    rc = krylov_alloc(K, std::vector<const kg_sector*>(n_t, s2), std::min(o->M, (int)d2), fin->nsm, o->schedule);
+    if (rc == KG_OK) {
+        for (auto& D : K.hdesc) D.tau = -h;
+        rc = krylov_upload(K, st);
+    }
+    if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
+    if (rc == KG_OK) rc = launch_reset_status(K, st);
+    const size_t pitch = (size_t)(K.M + 1) * d2 * sizeof(double2);
+    for (int ta = 1; rc == KG_OK && ta < n_t; ++ta) {
+        double2* row = V + (size_t)ta * n_t * d2;
+        if (cudaMemcpy2DAsync(K.vec(0, 0), pitch, row, d2 * sizeof(double2), d2 * sizeof(double2), n_t,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "four-time columns in", __FILE__, __LINE__);
+        if (rc == KG_OK) rc = grid_steps(R, ta, n_sub, st);
+        if (rc == KG_OK && cudaMemcpy2DAsync(row, d2 * sizeof(double2), K.vec(0, 0), pitch, d2 * sizeof(double2), n_t,
+                                             cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "four-time columns out", __FILE__, __LINE__);
+    }
+    if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+    if (rc == KG_OK) rc = block_status_of(K, "the four-time back-propagation");
+    R.release();
+    krylov_free(K);
+    return rc;
+}
+
+// The sector after applying op to s, or null when it does not exist.
+static int op_target(kg_sector* s, FourOp op, kg_sector** out) {
+    *out = nullptr;
+    const int nu = s->nu + (op.spin == 0 ? (op.dagger ? 1 : -1) : 0);
+    const int nd = s->nd + (op.spin == 1 ? (op.dagger ? 1 : -1) : 0);
+    if (nu < 0 || nd < 0 || nu > s->L || nd > s->L) return KG_OK;
+    return neighbour(s, op.spin, op.dagger, out);
+}
+
+int green_four_time(kg_sector* ini, kg_sector* fin, const int* ops, double dt, int n_t, const kg_opts* o, double* G) {
+    if (!ops || !G || n_t < 1 || !(dt >= 0.0) || !std::isfinite(dt)) {
+        set_error("bad four-time arguments");
+        return KG_EINVAL;
+    }
+    if (ini->L != fin->L || ini->nu != fin->nu || ini->nd != fin->nd) {
+        set_error("H_ini and H_fin must share (L, N_up, N_dn)");
+        return KG_EINVAL;
+    }
+    FourOp op[4];
+    for (int i = 0; i < 4; ++i) {
+        op[i] = FourOp{ops[3 * i], ops[3 * i + 1], ops[3 * i + 2]};
+        if (op[i].site < 0 || op[i].site >= fin->L || (op[i].spin & ~1) || (op[i].dagger & ~1)) {
+            set_error("operator %d: site in [0, L), spin and dagger 0 or 1", i);
+            return KG_EINVAL;
+        }
+    }
+    KG_TRY(check_opts(o));
+    const size_t nv = (size_t)n_t * n_t;
+    std::memset(G, 0, sizeof(double) * 2 * nv * nv);
+    // sectors of the right (A4 then A3) and the left (A1^dag then A2^dag) vectors
+    const FourOp l1op{op[0].site, op[0].spin, 1 - op[0].dagger}, l2op{op[1].site, op[1].spin, 1 - op[1].dagger};
+    kg_sector *r1 = nullptr, *r2 = nullptr, *l1 = nullptr, *l2 = nullptr;
+    KG_TRY(op_target(fin, op[3], &r1));
+    if (r1) KG_TRY(op_target(r1, op[2], &r2));
+    KG_TRY(op_target(fin, l1op, &l1));
+    if (l1) KG_TRY(op_target(l1, l2op, &l2));
+    if (!r2 || !l2 || r2->nu != l2->nu || r2->nd != l2->nd) return KG_OK;  // particle numbers not conserved
+    KG_TRY(ensure_gs(ini, o));
+    cudaStream_t st = pick_stream(fin, o);
+    const int n_sub = (o->dt_internal > 0.0) ? std::max(1, (int)std::lround(dt / o->dt_internal)) : 1;
+    const size_t d0 = (size_t)fin->d, d2 = (size_t)r2->d;
+    double2 *phi = nullptr, *Rv = nullptr, *Lv = nullptr, *Gd = nullptr;
+    auto done = [&](int r) {
+        cudaFree(phi);
+        cudaFree(Rv);
+        cudaFree(Lv);
+        cudaFree(Gd);
+        return r;
+    };
+    if (cudaMalloc(&phi, sizeof(double2) * n_t * d0) != cudaSuccess ||
+        cudaMalloc(&Rv, sizeof(double2) * nv * d2) != cudaSuccess ||
+        cudaMalloc(&Lv, sizeof(double2) * nv * d2) != cudaSuccess ||
+        cudaMalloc(&Gd, sizeof(double2) * nv * nv) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("four-time vectors: 2 x %zu vectors of dimension %zu do not fit", nv, d2);
+        return done(KG_ENOMEM);
+    }
+    // Phi(t_k) = e^{-iH t_k}|0>
+    int rc = cudaMemcpyAsync(phi, ini->gs, sizeof(double2) * d0, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                 ? KG_OK
+                 : cuda_fail(cudaGetLastError(), "Phi(0)", __FILE__, __LINE__);
+    if (rc == KG_OK && n_t > 1) {
+        Krylov K;
+        StepRunner R;
+        rc = krylov_alloc(K, {fin}, std::min(o->M, (int)d0), fin->nsm, o->schedule);
+        if (rc == KG_OK) {
+            K.hdesc[0].tau = dt / n_sub;
+            rc = krylov_upload(K, st);
+        }
+        if (rc == KG_OK && cudaMemcpyAsync(K.vec(0, 0), ini->gs, sizeof(double2) * d0, cudaMemcpyDeviceToDevice, st) !=
+                               cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "Phi start", __FILE__, __LINE__);
+        if (rc == KG_OK) rc = R.init(K, o->reorth, st, o->use_graphs != 0);
+        if (rc == KG_OK) rc = launch_reset_status(K, st);
+        for (int k = 1; rc == KG_OK && k < n_t; ++k) {
+            rc = grid_steps(R, 1, n_sub, st);
+            if (rc == KG_OK && cudaMemcpyAsync(phi + k * d0, K.vec(0, 0), sizeof(double2) * d0,
+                                               cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                rc = cuda_fail(cudaGetLastError(), "Phi(t_k)", __FILE__, __LINE__);
+        }
+        if (rc == KG_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? KG_OK : KG_ECUDA;
+        if (rc == KG_OK) rc = block_status_of(K, "step (ii)");
+        R.release();
+        krylov_free(K);
+    }
+    if (rc == KG_OK) rc = pair_vectors(fin, r1, r2, op[3], op[2], phi, n_t, dt, n_sub, o, Rv, st);
+    if (rc == KG_OK) rc = pair_vectors(fin, l1, l2, l1op, l2op, phi, n_t, dt, n_sub, o, Lv, st);
+    // Gd[q * nv + p] = <L_p | R_q>, p = t2 n_t + t1, q = t3 n_t + t4
+    for (size_t p0 = 0; rc == KG_OK && p0 < nv; p0 += kMaxOv) {
+        const int np = (int)std::min<size_t>(kMaxOv, nv - p0);
+        rc = launch_inner_lib(Lv + p0 * d2, np, Rv, (int)nv, (int)d2, Gd + p0, (int)nv, st);
+    }
+    std::vector<double2> h(nv * nv);
+    if (rc == KG_OK && (cudaMemcpyAsync(h.data(), Gd, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        rc = cuda_fail(cudaGetLastError(), "four-time readback", __FILE__, __LINE__);
+    if (rc != KG_OK) return done(rc);
+    for (int k1 = 0; k1 < n_t; ++k1)
+        for (int k2 = 0; k2 < n_t; ++k2)
+            for (int k3 = 0; k3 < n_t; ++k3)
+                for (int k4 = 0; k4 < n_t; ++k4) {
+                    const double2 v = h[((size_t)k3 * n_t + k4) * nv + ((size_t)k2 * n_t + k1)];
+                    const size_t off = (((size_t)k1 * n_t + k2) * n_t + k3) * n_t + k4;
+                    G[2 * off] = v.x;
+                    G[2 * off + 1] = v.y;
+                }
+    return done(KG_OK);
+}
+
 }  // namespace kg
 
 extern "C" int kg_green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau,

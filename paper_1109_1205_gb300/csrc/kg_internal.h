@@ -321,6 +321,7 @@ int keldysh_phi(kg_keldysh* X, int k, double* phi_host, const double* phi_in);
 int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* planes, long long* budget);
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                   const kg_opts* o, double* G_les, double* G_gtr, const double* dparams = nullptr);
+int green_four_time(kg_sector* ini, kg_sector* fin, const int* ops, double dt, int n_t, const kg_opts* o, double* G);
 int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o);
 void set_capturing(bool on);
 bool profiling();

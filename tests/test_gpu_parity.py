@@ -277,6 +277,25 @@ def test_step_exponential_taylor_vs_eigen(M):
         assert np.max(np.abs(out[0] - ref)) < 1e-11
 
 
+@pytest.mark.parametrize("model", [W.hubbard_ring(14, 4.0, 7, 6), W.siam_chain(14, 3.0, 6, 7, field=0.5)],
+                         ids=["ring14_7_6", "chain14_6_7"])
+def test_hpsi_and_propagation_beyond_l2(model):
+    """Sectors whose vectors exceed the 129 MB L2 (d = 10,306,296, 165 MB;
+    D_up = 3432 or 3003, D_dn odd in one): the standalone kg_hpsi matches the
+    oracle's H*psi to 1e-12 relative and three propagation steps match the
+    oracle's Chebyshev propagation to 1e-11."""
+    s = kg.Sector(model)
+    o = oracle.Sector(model)
+    assert s.dim == 10_306_296 and 16 * s.dim > (129 << 20)
+    x = W.random_state(s.dim, 31)
+    y = torch.empty(s.dim, dtype=torch.complex128, device="cuda")
+    s.hpsi(dev(x), y, stream())
+    assert relerr(host(y), o.hpsi(x)) < 1e-12
+    xd = dev(x)
+    s.propagate(xd, 0.05, 3)
+    assert np.max(np.abs(host(xd) - o.propagate(x, 0.15))) < 1e-11
+
+
 def test_bad_schedule_rejected():
     s = kg.Sector(W.random_model(4, 2, 2, seed=1))
     with pytest.raises(kg.KGError):
