@@ -872,3 +872,147 @@ def green_four_time(ini, fin, ops, dt, n_t, gs=None, K=80, tol=1e-12):
                 for k4 in range(n_t):
                     G[k1, k2, k3, k4] = np.vdot(Lv[k2][k1], R[k3][k4])
     return G
+
+
+# ------------------------------------------------------------------ NE-CPT
+# Section 5: the nonequilibrium cluster-perturbation theory of the paper's
+# application, a cluster of L_c sites (impurity at site 0) coupled by the
+# hopping V between its last site and the first site of a non-interacting
+# bath chain.  Every function lives on the L-shaped contour 0 -> t_max -> 0 ->
+# -i beta, discretised by the trapezoidal rule: forward points t_j = j dt
+# (weight dt), backward points (weight -dt), imaginary points -i tau_k,
+# tau_k = k dtau (weight -i dtau), half weights at the ends of each branch.
+
+def contour(dt, n_t, beta, n_tau):
+    """Contour points as (kind, index, s, z, w): kind 0 forward, 1 backward,
+    2 imaginary; s the position along the contour (a later point has a
+    larger s; the branch ends t_max and 0 appear twice, the later copy on the
+    later branch); z the complex time; w the quadrature weight."""
+    dtau = beta / n_tau
+    pts = []
+    for j in range(n_t):
+        w = dt * (0.5 if j in (0, n_t - 1) else 1.0) if n_t > 1 else 0.0
+        pts.append((0, j, len(pts), complex(j * dt), w))
+    for j in range(n_t - 1, -1, -1):
+        w = -dt * (0.5 if j in (0, n_t - 1) else 1.0) if n_t > 1 else 0.0
+        pts.append((1, j, len(pts), complex(j * dt), w))
+    for k in range(n_tau + 1):
+        w = -1j * dtau * (0.5 if k in (0, n_tau) else 1.0)
+        pts.append((2, k, len(pts), complex(0.0, -k * dtau), w))
+    return pts
+
+
+def _ordered(s1, s2, later, earlier):
+    """The contour-ordered value from its two orderings (the mean on the
+    diagonal, where the two one-sided limits differ by the jump)."""
+    if s1 > s2:
+        return later
+    if s1 < s2:
+        return earlier
+    return 0.5 * (later + earlier)
+
+
+def cluster_contour_gf(ini, fin, spin, dt, n_t, beta, n_tau, mu=0.0):
+    """The cluster Green's function G'_{ij}(z, z') = -i <T_C c_i(z) c^dag_j(z')>
+    of one spin on the contour of length beta, at a temperature 1/beta low
+    enough that only the ground state |0> of H_ini (and, through the trace,
+    the lowest states of its neighbour sectors) contributes.  From the
+    zero-temperature components of Section 4:
+      real-real:  G^> (z later), G^< (z' later);
+      G(t, -i tau)  = G^right(t, tau) + conj(G^left_{ji}(beta - tau, t)),
+      G(-i tau, t)  = G^left(tau, t) + conj(G^right_{ji}(t, beta - tau)),
+      G(-i tau, -i tau') = i G^M_beta(tau - tau'), with
+      G^M_beta(tau) = G^M(tau) - G^M(tau - beta) for tau > 0 and
+      G^M_beta(-tau) = G^M(-tau) - G^M(beta - tau),
+    the second terms being the antiperiodic tails that the trace at inverse
+    temperature beta adds near the end of the imaginary branch (terms of
+    relative size e^{-beta gap} are dropped).  The mean of the two orderings
+    on the diagonal z = z'.  Returns [L_c, L_c, n_pts, n_pts]."""
+    L = fin["L"]
+    orbs = [(i, spin) for i in range(L)]
+    pts = contour(dt, n_t, beta, n_tau)
+    dtau = beta / n_tau
+    taus = dtau * np.arange(n_tau + 1)
+    sec = Sector(ini)
+    gs = sec.ground_state()
+    Gl, Gg, _ = green_keldysh(ini, fin, orbs, dt, n_t, gs=gs)
+    Gr, Glf, _ = green_mixed(ini, fin, orbs, dt, n_t, taus, mu, gs=gs)
+    Gp, Gm, _ = green_matsubara(ini, orbs, taus, mu, gs=gs)
+    n = len(pts)
+    G = np.zeros((L, L, n, n), dtype=np.complex128)
+    NT = n_tau
+
+    def GMb_pos(k):  # G^M_beta(tau_k)
+        return Gp[k] - Gm[NT - k]
+
+    def GMb_neg(k):  # G^M_beta(-tau_k)
+        return Gm[k] - Gp[NT - k]
+
+    for p, (k1, i1, s1, _, _) in enumerate(pts):
+        for q, (k2, i2, s2, _, _) in enumerate(pts):
+            if k1 < 2 and k2 < 2:
+                val = _ordered(s1, s2, Gg[i1, i2], Gl[i1, i2])
+            elif k1 < 2:  # real earlier than imaginary
+                val = Gr[i1, i2] + np.conj(Glf[NT - i2, i1]).T
+            elif k2 < 2:  # imaginary later than real
+                val = Glf[i1, i2] + np.conj(Gr[i2, NT - i1]).T
+            else:
+                if i1 > i2:
+                    val = 1j * GMb_pos(i1 - i2)
+                elif i1 < i2:
+                    val = 1j * GMb_neg(i2 - i1)
+                else:
+                    val = 1j * 0.5 * (GMb_pos(0) + GMb_neg(0))
+            G[:, :, p, q] = val
+    return G
+
+
+def bath_surface_gf(L_b, T_b, dt, n_t, beta, n_tau):
+    """g_00(z, z') of the first site of a chain of L_b sites with hopping -T_b
+    (on-site energy and chemical potential 0), Section 5 Eqs. (gb1), (gb2):
+    -i [e^{-i T (z - z')} (1 + e^{-beta T})^{-1}]_00 for z later and
+    +i [e^{-i T (z - z')} (e^{beta T} + 1)^{-1}]_00 for z' later, from the
+    eigen-decomposition of the hopping matrix T."""
+    h = -T_b * (np.eye(L_b, k=1) + np.eye(L_b, k=-1))
+    eps, phi = np.linalg.eigh(h)
+    w0 = phi[0] ** 2
+    pts = contour(dt, n_t, beta, n_tau)
+    z = np.array([p[3] for p in pts])
+    s = np.array([p[2] for p in pts])
+    a = np.exp(-1j * np.outer(z, eps))   # e^{-i eps z}
+    b = np.exp(1j * np.outer(z, eps))    # e^{+i eps z'}
+    f = 1.0 / (np.exp(beta * eps) + 1.0)
+    later = -1j * (a * (w0 * (1.0 - f))) @ b.T
+    earlier = 1j * (a * (w0 * f)) @ b.T
+    S1, S2 = np.meshgrid(s, s, indexing="ij")
+    return np.where(S1 > S2, later, np.where(S1 < S2, earlier, 0.5 * (later + earlier)))
+
+
+def necpt_occupations(ini, fin, L_b, T_b, V, dt, n_t, beta, n_tau, mu=0.0):
+    """Section 5, Eq. (cpteq): G = (G'^{-1} - V)^{-1} on the contour for the
+    cluster coupled at its last site to the bath by V.  The bath integrated
+    out, the cluster block obeys G = G' + G' * Delta * G, Delta = V^2 g_00 on
+    the last site, * the contour integral (trapezoidal weights W):
+        G_{Lj} = (1 - G'_{LL} W Delta W)^{-1} G'_{Lj},
+        G_{ij} = G'_{ij} + G'_{iL} W Delta W G_{Lj}.
+    Returns n[spin, k, i] = n_{i spin}(t_k) = -i G^<_{ii}(t_k, t_k) (the forward
+    point t_k against the backward point t_k) for the cluster sites."""
+    L = fin["L"]
+    pts = contour(dt, n_t, beta, n_tau)
+    W = np.diag([p[4] for p in pts])
+    Delta = V * V * bath_surface_gf(L_b, T_b, dt, n_t, beta, n_tau)
+    M = W @ Delta @ W
+    npt = len(pts)
+    fwd = [p for p, q in enumerate(pts) if q[0] == 0]            # t_0 .. t_max
+    bwd = [p for p, q in enumerate(pts) if q[0] == 1][::-1]      # t_0 .. t_max
+    out = np.zeros((2, n_t, L))
+    for spin in (0, 1):
+        Gc = cluster_contour_gf(ini, fin, spin, dt, n_t, beta, n_tau, mu)
+        Lst = L - 1
+        X = np.linalg.solve(np.eye(npt) - Gc[Lst, Lst] @ M, np.eye(npt))
+        for i in range(L):
+            GLi = X @ Gc[Lst, i]
+            Gii = Gc[i, i] + Gc[i, Lst] @ M @ GLi
+            for k in range(n_t):
+                out[spin, k, i] = (-1j * Gii[fwd[k], bwd[k]]).real
+    return out
