@@ -342,6 +342,7 @@ def run_ours(args):
         spectral["fig1"] = fig1_restarts()
         driven = driven_vs_quench(si, sf, opts)
         driven["four_time"] = four_time(si, sf, opts)
+        driven["necpt"] = necpt_fig5()
         if not args.no_c2_full:
             c2_full = c2_full_grid(si, sf, opts)
     if rank == 0 and world == 1 and args.c3:
@@ -479,6 +480,39 @@ def four_time(si, sf, opts, n_t=8):
             "seconds": round(sec, 2), "gsteps": gsteps, "gsteps_per_s": round(gsteps / sec, 1),
             "equal_time_values": [round(float(v.real), 12) for v in eq],
             "max_equal_time_imag": float(np.max(np.abs(eq.imag)))}
+
+
+def necpt_fig5(sizes=(4, 6), dt=0.05, t_max=5.0, beta=15.0, dtau=0.05, L_b=1000):
+    """The NE-CPT of the paper's application (Fig. 5 model: impurity chain
+    cluster of L_c sites, U = T = V = 1, field 0.2 on the impurity switched
+    off at t = 0, coupled to a 1000-site bath) through kg_necpt_occupations:
+    the initial moment m_1 = n_1up - n_1dn, the net moment of the first four
+    sites and its decay on a coarse grid, per cluster size; seconds per call
+    (cluster components on the GPU, contour LU on the device)."""
+    import numpy as np
+    import torch
+
+    import paper_1109_1205_gb300 as kg
+    import workloads as W
+    n_t = int(round(t_max / dt)) + 1
+    n_tau = int(round(beta / dtau))
+    out = {"workload": "NE-CPT, Fig. 5 model: L_b=%d bath, U=T=V=1, h=0.2 -> 0, dt=%g, t_max=%g, beta=%g, dtau=%g "
+                       "(%d contour points)" % (L_b, dt, t_max, beta, dtau, 2 * n_t + n_tau + 1), "clusters": {}}
+    for Lc in sizes:
+        si = kg.Sector(W.siam_chain(Lc, 1.0, Lc // 2, Lc // 2, field=0.2))
+        sf = kg.Sector(W.siam_chain(Lc, 1.0, Lc // 2, Lc // 2, field=0.0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = kg.kg_necpt_occupations(si, sf, L_b, 1.0, 1.0, dt, n_t, beta, n_tau)
+        sec = time.perf_counter() - t0
+        m = n[0] - n[1]
+        step = int(round(1.0 / dt))
+        out["clusters"][str(Lc)] = {
+            "seconds": round(sec, 2), "m1_t0": round(float(m[0, 0]), 5),
+            "sum_m_first4_t0": round(float(m[0, :min(4, Lc)].sum()), 5),
+            "sum_m_first4_every_t1": [round(float(m[k, :min(4, Lc)].sum()), 5) for k in range(0, n_t, step)],
+            "max_particle_hole_dev": float(np.max(np.abs(n[0] + n[1] - 1.0)))}
+    return out
 
 
 def c3_rows(n_t):
@@ -850,6 +884,7 @@ def main():
     ap.add_argument("--fourier-case", action="store_true",
                     help="only the damped Fourier transform extra (for ncu captures of k_fourier)")
     ap.add_argument("--driven-case", action="store_true", help="only the driven-H(t) extra on the c2 ring")
+    ap.add_argument("--necpt-case", action="store_true", help="only the NE-CPT extra, clusters of 4, 6 and 8 sites")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint comparisons")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=400)
@@ -872,6 +907,9 @@ def main():
         si, sf = kg.Sector(cfg["ini"]), kg.Sector(cfg["fin"])
         si.ground_state(opts)
         print(json.dumps({"driven_case": driven_vs_quench(si, sf, opts), "four_time": four_time(si, sf, opts)}))
+        return
+    if args.necpt_case:
+        print(json.dumps({"necpt_case": necpt_fig5(sizes=(4, 6, 8))}))
         return
     if args.fourier_case:
         import paper_1109_1205_gb300 as kg

@@ -434,6 +434,30 @@ int kg_keldysh_create_td(kg_sector* H_ini, kg_sector* H_fin, const int* orb, int
 int kg_green_four_time(kg_sector* H_ini, kg_sector* H_fin, const int* ops, double dt, int n_t, const kg_opts* o,
                        double* G);
 
+/* ---- nonequilibrium cluster-perturbation theory ---------------------------
+ * Section 5, Eq. (cpteq) with the bath of Eqs. (gb1), (gb2): the cluster of
+ * H_ini / H_fin (L sites; its last site L-1) coupled by the hopping V to the
+ * first site of a non-interacting chain of L_b sites with hopping -T_b
+ * (on-site energies and chemical potential 0; a half-filled, particle-hole
+ * symmetric bath).  G = (G'^{-1} - V)^{-1} is solved on the contour
+ * 0 -> t_max -> 0 -> -i beta, t_max = (n_t - 1) dt, discretised by the
+ * trapezoidal rule on t_k = k dt and tau_j = j beta / n_tau (2 n_t + n_tau + 1
+ * points, at most 3072).  The cluster functions at inverse temperature beta
+ * are built from the zero-temperature components of this library
+ * (kg_green_keldysh, kg_green_mixed, kg_green_matsubara_steps with mu = 0,
+ * opts as given) plus the antiperiodic tails of the imaginary branch; terms of
+ * relative size e^{-beta gap} of the cluster are dropped, so beta must be
+ * large against the inverse gap.  The bath integrated out, the coupled site's
+ * contour equation is solved by an LU factorisation on the device.
+ * n_out: host, [2][n_t][L] doubles, n_out[s][k][i] = n_{i s}(t_k) = -i
+ * G^<_{ii}(t_k, t_k) of the coupled system (spin s = 0 up, 1 down).
+ * KG_EINVAL for bad sizes (L_b < 1, n_t < 1, n_tau < 2, dt < 0, beta <= 0,
+ * non-finite values, too many contour points) or differing sectors;
+ * KG_ENUMERIC if the contour matrix is singular; the errors of the component
+ * calls otherwise.  Discretisation error: second order in dt and dtau. */
+int kg_necpt_occupations(kg_sector* H_ini, kg_sector* H_fin, int L_b, double T_b, double V, double dt, int n_t,
+                         double beta, int n_tau, const kg_opts* o, double* n_out);
+
 /* ---- mixed components on the imaginary branch ---------------------------
  * Section 4, the remark after step (iv): the components of the contour
  * Green's function with one time on the imaginary branch, at zero

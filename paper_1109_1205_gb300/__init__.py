@@ -18,5 +18,5 @@ from ._lib import (  # noqa: F401
     kg_probe_fp64, kg_overlaps, kg_green_equilibrium_batched, kg_green_equilibrium_vjp, kg_green_lanczos,
     kg_green_equilibrium_fine, kg_green_fourier, kg_overlaps_noalloc, kg_green_matsubara,
     kg_green_matsubara_steps, kg_green_mixed, kg_green_restarted, kg_green_keldysh_td, kg_keldysh_create_td,
-    kg_green_four_time,
+    kg_green_four_time, kg_necpt_occupations,
 )

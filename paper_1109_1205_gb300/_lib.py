@@ -75,6 +75,7 @@ _sig = {
     "kg_keldysh_create": (_I, [_P, _P, _P, _I, _D, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_keldysh_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_four_time": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(Opts), _P]),
+    "kg_necpt_occupations": (_I, [_P, _P, _I, _D, _D, _D, _I, _D, _I, ctypes.POINTER(Opts), _P]),
     "kg_keldysh_create_td": (_I, [_P, _P, _P, _I, _D, _I, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "kg_green_mixed": (_I, [_P, _P, _P, _I, _D, _I, _D, _D, _I, ctypes.POINTER(Opts), _P, _P]),
     "kg_green_restarted": (_I, [_P, _P, _I, _I, _I, _I, _D, ctypes.POINTER(Opts), _P, _P]),
@@ -380,6 +381,16 @@ def kg_green_four_time(h_ini, h_fin, ops, dt, n_t, opts=None):
     _check(lib.kg_green_four_time(h_ini, h_fin, op.ctypes.data, float(dt), int(n_t), ctypes.byref(o),
                                   G.ctypes.data), "kg_green_four_time")
     return G
+
+
+def kg_necpt_occupations(ini, fin, L_b, T_b, V, dt, n_t, beta, n_tau, opts=None):
+    """NE-CPT occupations n[spin, k, i] of the cluster sites (Sector objects
+    ini, fin) coupled to the bath chain (Section 5), on t_k = k dt."""
+    o = opts if opts is not None else kg_opts_default()
+    out = np.zeros((2, int(n_t), fin.L))
+    _check(lib.kg_necpt_occupations(ini.handle, fin.handle, int(L_b), float(T_b), float(V), float(dt), int(n_t),
+                                    float(beta), int(n_tau), ctypes.byref(o), out.ctypes.data), "kg_necpt_occupations")
+    return out
 
 
 def kg_keldysh_create_td(h_ini, h_fin, orbitals, dt, n_t, dparams, opts=None):

@@ -322,6 +322,12 @@ int keldysh_plan(const kg_keldysh* X, int* phi_on_host, int* stores_kept, int* p
 int green_keldysh(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t,
                   const kg_opts* o, double* G_les, double* G_gtr, const double* dparams = nullptr);
 int green_four_time(kg_sector* ini, kg_sector* fin, const int* ops, double dt, int n_t, const kg_opts* o, double* G);
+int green_mixed(kg_sector* ini, kg_sector* fin, const int* orb, int n_orb, double dt, int n_t, double mu, double dtau,
+                int n_tau, const kg_opts* o, double* G_right, double* G_left);
+int green_matsubara_steps(kg_sector* s, const int* orb, int n_orb, double mu, double dtau, int n_steps,
+                          const kg_opts* o, double* G_plus, double* G_minus);
+int necpt_occupations(kg_sector* ini, kg_sector* fin, int L_b, double T_b, double V, double dt, int n_t, double beta,
+                      int n_tau, const kg_opts* o, double* n_out);
 int propagate(kg_sector* s, double2* x, double dt, int n_steps, const kg_opts* o);
 void set_capturing(bool on);
 bool profiling();
