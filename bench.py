@@ -342,7 +342,7 @@ def run_ours(args):
         spectral["fig1"] = fig1_restarts()
         driven = driven_vs_quench(si, sf, opts)
         driven["four_time"] = four_time(si, sf, opts)
-        driven["necpt"] = necpt_fig5()
+        driven["necpt"] = necpt_fig5(sizes=(4,), dtau=0.1)
         if not args.no_c2_full:
             c2_full = c2_full_grid(si, sf, opts)
     if rank == 0 and world == 1 and args.c3:
