@@ -1119,7 +1119,7 @@ static void block_release(KBlock& B) {
 
 // ------------------------------------------------------- driven H(t)
 // Section 6 proposes commutator-free exponential propagators for a
-// Hamiltonian with a general time dependence after t = 0.  This build takes
+// Hamiltonian with a general time dependence after t = 0.  The library takes
 // the fourth-order one with two exponentials: with A_1, A_2 the Hamiltonian
 // at the two Gauss-Legendre nodes t + (1/2 -+ sqrt(3)/6) h of a step,
 //   U(t + h, t) = exp(-i h (a1 A_1 + a2 A_2)) exp(-i h (a2 A_1 + a1 A_2)),
