@@ -166,6 +166,11 @@ def test_every_handle_entry_rejects_null(kg):
     assert lib.kg_green_matsubara(None, orb.ctypes.data, 1, 10, 0.0, b, 1, ob, b, b) == E
     assert lib.kg_green_matsubara_steps(None, orb.ctypes.data, 1, 0.0, 0.1, 1, ob, b, b) == E
     assert lib.kg_probe_fp64(None, None) == E
+    assert lib.kg_green_keldysh_td(None, None, orb.ctypes.data, 1, 0.1, 3, b, ob, b, b) == E
+    assert lib.kg_keldysh_create_td(None, None, orb.ctypes.data, 1, 0.1, 3, b, ob, None) == E
+    ops = np.zeros(12, dtype=np.int32)
+    assert lib.kg_green_four_time(None, None, ops.ctypes.data, 0.1, 2, ob, b) == E
+    assert lib.kg_necpt_occupations(None, None, 10, 1.0, 1.0, 0.1, 2, 15.0, 10, ob, b) == E
     lib.kg_free_sector(None)
     lib.kg_keldysh_free(None)
     lib.kg_opts_default(None)
