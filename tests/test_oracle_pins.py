@@ -1069,3 +1069,15 @@ def test_necpt_particle_hole_symmetry():
         n = oracle.necpt_occupations(ini, fin, 100, 1.0, 1.0, dt, n_t, 15.0, int(round(15.0 / dt)))
         dev.append(np.max(np.abs(n[0] + n[1] - 1.0)))
     assert dev[1] < 3e-3 and dev[0] / dev[1] > 3.0, dev
+
+
+def test_four_time_equilibrium_depends_on_differences_only():
+    """Without a quench (H_ini = H_fin) the four-time function depends only on
+    the time differences: shifting all four times by one grid step leaves it
+    unchanged (the ground state is stationary)."""
+    m = W.random_model(4, 2, 1, seed=5, complex_hopping=True)
+    ops = [(1, 0, 0), (2, 1, 1), (0, 1, 0), (3, 0, 1)]
+    G = oracle.green_four_time(m, m, ops, 0.2, 4)
+    assert np.max(np.abs(G)) > 1e-3
+    for k in np.ndindex(3, 3, 3, 3):
+        assert abs(G[k] - G[tuple(x + 1 for x in k)]) < 1e-12
