@@ -22,7 +22,12 @@ exactly as the paper defines them:
   rule on the sampled times);
 * the Matsubara and mixed components named after step (iv) of Section 4, at
   zero temperature with a chemical potential mu on the imaginary branch
-  (imaginary-time propagators from dense eigen-decompositions, small sectors).
+  (imaginary-time propagators from dense eigen-decompositions, small sectors);
+* the NE-CPT of Section 5 (Eq. (cpteq), the bath of Eqs. (gb1), (gb2)) on a
+  trapezoidal Keldysh-Matsubara contour;
+* the two directions of the outlook in Section 6: a driven H(t) by the
+  fourth-order commutator-free exponential step, and four-time correlation
+  functions.
 
 Every propagation here is a Chebyshev expansion over the whole interval
 (never the GPU's restarted Krylov steps), so the two sides are independent.
